@@ -1,0 +1,189 @@
+/*
+ * eofa.h -- C ABI of the GB300 library for the exact one-flavor algorithm
+ * (EOFA) with Shamir / Moebius domain-wall fermions.
+ *
+ * Paper: D. Murphy, "Domain Wall Fermion Simulations with the Exact
+ * One-Flavor Algorithm", Lattice 2016.  Equation numbers below are the
+ * paper's: Eq. (3) D_DWF = D_EOFA * D-tilde, Eq. (5) the EOFA action,
+ * Eq. (7) the pseudofermion force, Eq. (8) the EOFA linear systems.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Lattice dims[4] = {X, Y, Z, T}, every extent even (even-odd
+ * decomposition, Sec. 5.1).  Site index i = x + X (y + Y (z + Z t)).
+ * Complex numbers are interleaved (re, im) FP64.  Host canonical layouts:
+ *   gauge U   [i][mu][a][b]            mu = x, y, z, t -> 0..3     (4 V 9 cplx)
+ *   5D field  [s][i][spin][colour]     s = 0..Ls-1                  (12 V Ls cplx)
+ *   4D field  [i][spin][colour]                                     (12 V cplx)
+ *   force F   [i][mu][a][b]            traceless Hermitian           (4 V 9 cplx)
+ * Gamma matrices: Euclidean chiral basis, gamma_5 = diag(1, 1, -1, -1),
+ * so P_+ keeps spins 0, 1 and P_- keeps spins 2, 3.
+ * D_w = (4 - M5) - 1/2 sum_mu [(1 - g_mu) U_mu(x) psi(x+mu)
+ *                              + (1 + g_mu) U_mu(x-mu)^+ psi(x-mu)],
+ * periodic in x, y, z; the t-links from T-1 to 0 carry bc_t (+1 or -1).
+ * L = P_+ L_+ + P_- L_-, (L_+)_{s,s-1} = 1, (L_+)_{0,Ls-1} = -m_f, L_- = L_+^T.
+ * Moebius weights c = alpha/2, d = 1/2 (Shamir: alpha = 1).
+ *
+ * Ownership and errors
+ * --------------------
+ * Host pointers are caller-owned and only read or written during the call.
+ * "_dev" calls take device pointers (caller-owned, same canonical layout)
+ * and a cudaStream_t passed as void*; they are stream-ordered and return once
+ * the work is queued unless they must read a scalar back (solves, action).
+ * Every call returns EOFA_OK (0) or a negative status and never throws;
+ * eofa_last_error() gives a message for the last failure on the context.
+ */
+#ifndef EOFA_H
+#define EOFA_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define EOFA_OK 0
+#define EOFA_EINVAL (-1)    /* bad argument: dims, Ls, masses, pointers, non-unitary U */
+#define EOFA_ENOMEM (-2)    /* device allocation failed */
+#define EOFA_ENOTCONV (-3)  /* solver hit maxiter; info still filled */
+#define EOFA_ENUMERIC (-4)  /* NaN or Inf met */
+#define EOFA_ETIMEOUT (-5)  /* device watchdog expired */
+#define EOFA_EDEVICE (-6)   /* CUDA error; message has the CUDA string */
+
+/* storage / arithmetic of the solver's inner iteration */
+#define EOFA_PREC_F64 0         /* FP64 storage, FP64 arithmetic */
+#define EOFA_PREC_MIXED_F32 1   /* inner FP32 storage + arithmetic, FP64 reliable updates */
+#define EOFA_PREC_MIXED_F16 2   /* inner FP16 storage (per-site FP32 scale), FP32 arithmetic */
+
+/* which linear system eofa_solve inverts */
+#define EOFA_SYS_DWF 0     /* D_DWF(m_f) x = b                        (Eq. (3)) */
+#define EOFA_SYS_EOFA_L 1  /* (H(m1) + shift Delta_- P_-) x = b       (Eq. (8)) */
+#define EOFA_SYS_EOFA_R 2  /* (H(m2) + shift Delta_+ P_+) x = b       (Eq. (8)) */
+
+typedef struct eofa_ctx eofa_ctx;
+
+typedef struct {
+    int Ls;           /* fifth-dimension extent; must equal the context's */
+    double alpha;     /* Moebius scale (c = alpha/2, d = 1/2) */
+    double M5;        /* domain-wall height */
+    int system;       /* EOFA_SYS_* */
+    double mf;        /* mass of EOFA_SYS_DWF */
+    double m1, m2;    /* EOFA mass pair (m1 < m2) for EOFA_SYS_EOFA_L/R */
+    double shift;     /* a in (H + a Delta P); the action's chi_R uses -1 */
+    int precision;    /* EOFA_PREC_* */
+    double tol;       /* target true relative residual |b - A x| / |b| */
+    int maxiter;      /* cap on inner iterations (all restarts) */
+    double delta;     /* reliable-update threshold (mixed precision), e.g. 0.1 */
+    int use_x0;       /* 1: x holds the initial guess on entry */
+} eofa_solve_params;
+
+typedef struct {
+    int iters;             /* inner CG iterations */
+    int reliable_updates;  /* FP64 residual recomputations */
+    double true_resid;     /* FP64 |b - A x| / |b| of the full (unpreconditioned) system */
+    double seconds;        /* wall time of the solve */
+    int status;            /* EOFA_OK or the failure */
+} eofa_solve_info;
+
+/* Create a context for one lattice.  dims: {X, Y, Z, T}, all even and >= 2;
+ * Ls in [1, 64]; bc_t = +1 or -1; flags must be 0.  Picks the current CUDA
+ * device.  (Sec. 2 notation: V = X Y Z T, Ls.) */
+int eofa_create(eofa_ctx** ctx, const int dims[4], int Ls, int bc_t, int flags);
+int eofa_destroy(eofa_ctx* ctx);
+const char* eofa_last_error(const eofa_ctx* ctx);
+
+/* Load the gauge field (Sec. 2: U_mu(x) inside D_w).  U: host canonical,
+ * copied.  Checks |U^+ U - 1| < 1e-10 on every link (else EOFA_EINVAL). */
+int eofa_gauge_load(eofa_ctx* ctx, const double* U);
+int eofa_gauge_load_dev(eofa_ctx* ctx, const double* U_dev, void* stream);
+
+/* out = D_DWF in (dagger = 0) or D_DWF^+ in (dagger = 1), full 5D lattice,
+ * Eq. (3) first line.  in, out: 5D canonical, 12 V Ls complex each. */
+int eofa_dwf_apply(eofa_ctx* ctx, int Ls, double alpha, double M5, double mf, int dagger,
+                   const double* in, double* out);
+int eofa_dwf_apply_dev(eofa_ctx* ctx, int Ls, double alpha, double M5, double mf, int dagger,
+                       const double* in_dev, double* out_dev, void* stream);
+
+/* out = D_EOFA in, Eq. (3) middle line: D_w + (1 - L) D-tilde^{-1} (the
+ * 5D-local inverse is applied in O(Ls), never as a dense matrix). */
+int eofa_eofa_apply(eofa_ctx* ctx, int Ls, double alpha, double M5, double mf,
+                    const double* in, double* out);
+int eofa_eofa_apply_dev(eofa_ctx* ctx, int Ls, double alpha, double M5, double mf,
+                        const double* in_dev, double* out_dev, void* stream);
+
+/* Even-odd hop on every s-slice, the hopping part of D_w (Sec. 2):
+ * out(x, s) = -1/2 sum_mu [...] restricted to output sites of parity
+ * out_parity, for a 5D field stored in the library's device layout of the
+ * given storage precision (EOFA_PREC_F64 / MIXED_F32 / MIXED_F16 selects
+ * FP64 / FP32 / FP16+scale).  For benchmarking and kernel tests: in_dev and
+ * out_dev are device buffers of eofa_field_bytes(ctx, precision) bytes. */
+long long eofa_field_bytes(const eofa_ctx* ctx, int precision);
+int eofa_hop_dev(eofa_ctx* ctx, int precision, int out_parity, int dagger,
+                 const void* in_dev, void* out_dev, void* stream);
+/* Pack a canonical FP64 5D field (device) into the two half-checkerboard
+ * device-layout fields of the given precision, and back. */
+int eofa_pack_dev(eofa_ctx* ctx, int precision, const double* canon_dev, void* even_dev,
+                  void* odd_dev, void* stream);
+int eofa_unpack_dev(eofa_ctx* ctx, int precision, const void* even_dev, const void* odd_dev,
+                    double* canon_dev, void* stream);
+
+/* Solve one linear system (Sec. 5.1): even-odd Schur complement, 5D-local
+ * inverse through the Cayley factorisation of Eq. (3), CG on the normal
+ * equations, optional mixed precision with FP64 reliable updates.
+ * b, x: 5D canonical (x is the initial guess when p->use_x0).  Returns
+ * EOFA_ENOTCONV with info filled when tol is not reached in maxiter. */
+int eofa_solve(eofa_ctx* ctx, const eofa_solve_params* p, const double* b, double* x,
+               eofa_solve_info* info);
+int eofa_solve_dev(eofa_ctx* ctx, const eofa_solve_params* p, const double* b_dev, double* x_dev,
+                   eofa_solve_info* info, void* stream);
+
+/* EOFA action S_f = phi^+ M_EOFA phi, Eq. (5), for a 4D pseudofermion phi.
+ * Needs m1 < m2.  Runs the two solves chi_L, chi_R (info[0], info[1]) with
+ * the given precision and tol; S is accumulated in FP64. */
+int eofa_action(eofa_ctx* ctx, int Ls, double alpha, double M5, double m1, double m2,
+                int precision, double tol, const double* phi, double* S, eofa_solve_info info[2]);
+int eofa_action_dev(eofa_ctx* ctx, int Ls, double alpha, double M5, double m1, double m2,
+                    int precision, double tol, const double* phi_dev, double* S,
+                    eofa_solve_info info[2], void* stream);
+
+/* EOFA pseudofermion force, Eq. (7): F_mu(x) = sum_a F^a T^a with
+ * F^a = dS_f / dw for U_mu(x) -> exp(i w T^a) U_mu(x), T^a = lambda^a / 2.
+ * F: 4 V 3x3 traceless Hermitian, canonical.  S (may be NULL) gets the
+ * action from the same solves. */
+int eofa_force(eofa_ctx* ctx, int Ls, double alpha, double M5, double m1, double m2,
+               int precision, double tol, const double* phi, double* F, double* S,
+               eofa_solve_info info[2]);
+int eofa_force_dev(eofa_ctx* ctx, int Ls, double alpha, double M5, double m1, double m2,
+                   int precision, double tol, const double* phi_dev, double* F_dev, double* S,
+                   eofa_solve_info info[2], void* stream);
+
+/* Force from given solutions (Eq. (7) with chi_L, chi_R supplied):
+ * F = k T[chi_L] - k T[chi_R], chi: 5D canonical device fields. */
+int eofa_force_from_chi_dev(eofa_ctx* ctx, double k, const double* chiL_dev,
+                            const double* chiR_dev, double* F_dev, void* stream);
+
+/* Gradient of S with respect to the real and imaginary parts of every link
+ * entry (for automatic differentiation): G has the gauge layout and holds
+ * dS/dRe U + i dS/dIm U.  Uses the same chi_L, chi_R as the force. */
+int eofa_grad_from_chi_dev(eofa_ctx* ctx, double k, const double* chiL_dev,
+                           const double* chiR_dev, double* G_dev, void* stream);
+
+/* EOFA coefficients (Sec. 2): k and Omega_pm with Delta_pm = k Omega Omega^T.
+ * Omega_plus, Omega_minus: host arrays of Ls doubles (may be NULL). */
+int eofa_coefficients(int Ls, double alpha, double m1, double m2, double* k,
+                      double* Omega_plus, double* Omega_minus);
+
+/* Molecular dynamics link update U <- exp(i eps P) U on the device gauge
+ * field of the context and on the canonical copy U_dev (if not NULL);
+ * P: 4 V traceless Hermitian 3x3, canonical, device. */
+int eofa_link_update_dev(eofa_ctx* ctx, double eps, const double* P_dev, double* U_dev,
+                         void* stream);
+
+/* Batched solves: n systems on n contexts (contexts may share a lattice),
+ * iterated together in one CUDA-graph-captured loop.  b[i], x[i]: 5D
+ * canonical host buffers of context ctxs[i]. */
+int eofa_solve_batched(eofa_ctx* const* ctxs, int n, const eofa_solve_params* params,
+                       const double* const* b, double* const* x, eofa_solve_info* info);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EOFA_H */

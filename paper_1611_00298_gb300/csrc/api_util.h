@@ -1,0 +1,16 @@
+// Helpers shared by the C-ABI translation units.
+#pragma once
+#include "ops.h"
+
+int fail(eofa_ctx* ctx, int code, const std::string& msg);
+void check_ls(const eofa_ctx* ctx, int Ls);
+void require_gauge(const eofa_ctx* ctx);
+
+void apply_dwf_fields(eofa_ctx* ctx, const Coeffs& c, int dagger, const void* in_e, const void* in_o, void* out_e,
+                      void* out_o, cudaStream_t st);
+void apply_eofa_fields(eofa_ctx* ctx, const Op5& G, const void* in_e, const void* in_o, void* out_e, void* out_o,
+                       cudaStream_t st);
+
+// one solve on device canonical buffers (solver.cu)
+int solve_dev_impl(eofa_ctx* ctx, const eofa_solve_params* p, const double* b_dev, double* x_dev,
+                   eofa_solve_info* info, cudaStream_t st);

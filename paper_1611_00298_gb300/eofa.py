@@ -1,0 +1,308 @@
+"""Thin ctypes binding of libeofa (include/eofa.h).
+
+Argument marshalling only: every operator, solve, reduction and force runs
+in the CUDA kernels of libeofa.  Host-buffer calls take numpy complex128
+arrays in the canonical layouts; "_dev" calls take CUDA torch tensors
+(complex128 or float64 views of the same layout) and use the current torch
+stream.  There is no CPU fallback: if the library is not built or no GPU is
+present the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libeofa.so")
+
+OK, EINVAL, ENOMEM, ENOTCONV, ENUMERIC, ETIMEOUT, EDEVICE = 0, -1, -2, -3, -4, -5, -6
+PREC_F64, PREC_MIXED_F32, PREC_MIXED_F16 = 0, 1, 2
+SYS_DWF, SYS_EOFA_L, SYS_EOFA_R = 0, 1, 2
+
+# every symbol declared in include/eofa.h
+EXPORTS = [
+    "eofa_create", "eofa_destroy", "eofa_last_error", "eofa_gauge_load", "eofa_gauge_load_dev",
+    "eofa_dwf_apply", "eofa_dwf_apply_dev", "eofa_eofa_apply", "eofa_eofa_apply_dev",
+    "eofa_field_bytes", "eofa_hop_dev", "eofa_pack_dev", "eofa_unpack_dev",
+    "eofa_solve", "eofa_solve_dev", "eofa_action", "eofa_action_dev", "eofa_force", "eofa_force_dev",
+    "eofa_force_from_chi_dev", "eofa_grad_from_chi_dev", "eofa_coefficients", "eofa_link_update_dev",
+    "eofa_solve_batched",
+]
+
+
+class EOFAError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"libeofa error {code}: {msg}")
+        self.code = code
+
+
+class SolveParams(ctypes.Structure):
+    _fields_ = [("Ls", ctypes.c_int), ("alpha", ctypes.c_double), ("M5", ctypes.c_double),
+                ("system", ctypes.c_int), ("mf", ctypes.c_double), ("m1", ctypes.c_double),
+                ("m2", ctypes.c_double), ("shift", ctypes.c_double), ("precision", ctypes.c_int),
+                ("tol", ctypes.c_double), ("maxiter", ctypes.c_int), ("delta", ctypes.c_double),
+                ("use_x0", ctypes.c_int)]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("reliable_updates", ctypes.c_int), ("true_resid", ctypes.c_double),
+                ("seconds", ctypes.c_double), ("status", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libeofa.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with paper_1611_00298_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    P, I, D, LL = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_longlong
+    sig = {
+        "eofa_create": (I, [ctypes.POINTER(P), ctypes.POINTER(I), I, I, I]),
+        "eofa_destroy": (I, [P]),
+        "eofa_last_error": (ctypes.c_char_p, [P]),
+        "eofa_gauge_load": (I, [P, P]),
+        "eofa_gauge_load_dev": (I, [P, P, P]),
+        "eofa_dwf_apply": (I, [P, I, D, D, D, I, P, P]),
+        "eofa_dwf_apply_dev": (I, [P, I, D, D, D, I, P, P, P]),
+        "eofa_eofa_apply": (I, [P, I, D, D, D, P, P]),
+        "eofa_eofa_apply_dev": (I, [P, I, D, D, D, P, P, P]),
+        "eofa_field_bytes": (LL, [P, I]),
+        "eofa_hop_dev": (I, [P, I, I, I, P, P, P]),
+        "eofa_pack_dev": (I, [P, I, P, P, P, P]),
+        "eofa_unpack_dev": (I, [P, I, P, P, P, P]),
+        "eofa_solve": (I, [P, ctypes.POINTER(SolveParams), P, P, ctypes.POINTER(SolveInfo)]),
+        "eofa_solve_dev": (I, [P, ctypes.POINTER(SolveParams), P, P, ctypes.POINTER(SolveInfo), P]),
+        "eofa_action": (I, [P, I, D, D, D, D, I, D, P, ctypes.POINTER(D), ctypes.POINTER(SolveInfo)]),
+        "eofa_action_dev": (I, [P, I, D, D, D, D, I, D, P, ctypes.POINTER(D), ctypes.POINTER(SolveInfo), P]),
+        "eofa_force": (I, [P, I, D, D, D, D, I, D, P, P, ctypes.POINTER(D), ctypes.POINTER(SolveInfo)]),
+        "eofa_force_dev": (I, [P, I, D, D, D, D, I, D, P, P, ctypes.POINTER(D), ctypes.POINTER(SolveInfo), P]),
+        "eofa_force_from_chi_dev": (I, [P, D, P, P, P, P]),
+        "eofa_grad_from_chi_dev": (I, [P, D, P, P, P, P]),
+        "eofa_coefficients": (I, [I, D, D, D, ctypes.POINTER(D), P, P]),
+        "eofa_link_update_dev": (I, [P, D, P, P, P]),
+        "eofa_solve_batched": (I, [ctypes.POINTER(P), I, ctypes.POINTER(SolveParams), ctypes.POINTER(P),
+                                   ctypes.POINTER(P), ctypes.POINTER(SolveInfo)]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _ptr(a) -> int:
+    """Address of a numpy array (C-contiguous) or a torch tensor."""
+    if isinstance(a, np.ndarray):
+        assert a.flags["C_CONTIGUOUS"], "arrays must be C-contiguous"
+        return a.ctypes.data
+    assert a.is_contiguous(), "tensors must be contiguous"
+    return a.data_ptr()
+
+
+def _stream():
+    import torch
+    return torch.cuda.current_stream().cuda_stream
+
+
+def coefficients(Ls, alpha, m1, m2):
+    """(k, Omega_+, Omega_-) of the EOFA rank-one factorisation (libeofa)."""
+    lib = load_library()
+    k = ctypes.c_double()
+    Op = np.zeros(Ls)
+    Om = np.zeros(Ls)
+    rc = lib.eofa_coefficients(Ls, alpha, m1, m2, ctypes.byref(k), Op.ctypes.data, Om.ctypes.data)
+    if rc != OK:
+        raise EOFAError(rc, "eofa_coefficients")
+    return k.value, Op, Om
+
+
+@dataclass
+class Params:
+    alpha: float = 2.0
+    M5: float = 1.8
+
+
+class Lattice:
+    """One lattice (dims = (X, Y, Z, T), Ls, time boundary phase) on the current GPU."""
+
+    def __init__(self, dims, Ls, bc_t=-1):
+        self.lib = load_library()
+        self.dims = tuple(int(d) for d in dims)
+        self.Ls = int(Ls)
+        self.bc_t = int(bc_t)
+        X, Y, Z, T = self.dims
+        self.V = X * Y * Z * T
+        self.ctx = ctypes.c_void_p()
+        arr = (ctypes.c_int * 4)(*self.dims)
+        rc = self.lib.eofa_create(ctypes.byref(self.ctx), arr, self.Ls, self.bc_t, 0)
+        if rc != OK:
+            raise EOFAError(rc, "eofa_create failed (bad dims/Ls/bc or no CUDA device)")
+
+    def close(self):
+        if self.ctx:
+            self.lib.eofa_destroy(self.ctx)
+            self.ctx = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc, what):
+        if rc != OK:
+            msg = self.lib.eofa_last_error(self.ctx)
+            raise EOFAError(rc, f"{what}: {msg.decode() if msg else ''}")
+
+    # -- shapes
+    @property
+    def shape5(self):
+        X, Y, Z, T = self.dims
+        return (self.Ls, T, Z, Y, X, 4, 3)
+
+    @property
+    def shape4(self):
+        X, Y, Z, T = self.dims
+        return (T, Z, Y, X, 4, 3)
+
+    @property
+    def shapeU(self):
+        X, Y, Z, T = self.dims
+        return (T, Z, Y, X, 4, 3, 3)
+
+    # -- host-buffer calls
+    def gauge_load(self, U):
+        U = np.ascontiguousarray(U, dtype=np.complex128)
+        assert U.shape == self.shapeU
+        self._check(self.lib.eofa_gauge_load(self.ctx, _ptr(U)), "gauge_load")
+
+    def gauge_load_dev(self, U):
+        self._check(self.lib.eofa_gauge_load_dev(self.ctx, _ptr(U), _stream()), "gauge_load_dev")
+
+    def dwf_apply(self, psi, alpha, M5, mf, dagger=False):
+        psi = np.ascontiguousarray(psi, dtype=np.complex128)
+        out = np.empty_like(psi)
+        self._check(self.lib.eofa_dwf_apply(self.ctx, self.Ls, alpha, M5, mf, int(dagger), _ptr(psi), _ptr(out)),
+                     "dwf_apply")
+        return out
+
+    def eofa_apply(self, psi, alpha, M5, mf):
+        psi = np.ascontiguousarray(psi, dtype=np.complex128)
+        out = np.empty_like(psi)
+        self._check(self.lib.eofa_eofa_apply(self.ctx, self.Ls, alpha, M5, mf, _ptr(psi), _ptr(out)), "eofa_apply")
+        return out
+
+    def solve_params(self, system=SYS_DWF, alpha=2.0, M5=1.8, mf=0.0, m1=0.0, m2=0.0, shift=0.0,
+                     precision=PREC_F64, tol=1e-10, maxiter=100000, delta=0.1, use_x0=False):
+        return SolveParams(self.Ls, alpha, M5, system, mf, m1, m2, shift, precision, tol, maxiter, delta,
+                           int(use_x0))
+
+    def solve(self, b, x0=None, **kw):
+        b = np.ascontiguousarray(b, dtype=np.complex128)
+        p = self.solve_params(use_x0=x0 is not None, **kw)
+        x = np.zeros_like(b) if x0 is None else np.ascontiguousarray(x0, dtype=np.complex128).copy()
+        info = SolveInfo()
+        rc = self.lib.eofa_solve(self.ctx, ctypes.byref(p), _ptr(b), _ptr(x), ctypes.byref(info))
+        self._check(rc, "solve")
+        return x, info
+
+    def action(self, phi, alpha, M5, m1, m2, precision=PREC_F64, tol=1e-10):
+        phi = np.ascontiguousarray(phi, dtype=np.complex128)
+        S = ctypes.c_double()
+        info = (SolveInfo * 2)()
+        rc = self.lib.eofa_action(self.ctx, self.Ls, alpha, M5, m1, m2, precision, tol, _ptr(phi), ctypes.byref(S),
+                                  info)
+        self._check(rc, "action")
+        return S.value, info
+
+    def force(self, phi, alpha, M5, m1, m2, precision=PREC_F64, tol=1e-10):
+        phi = np.ascontiguousarray(phi, dtype=np.complex128)
+        F = np.empty(self.shapeU, dtype=np.complex128)
+        S = ctypes.c_double()
+        info = (SolveInfo * 2)()
+        rc = self.lib.eofa_force(self.ctx, self.Ls, alpha, M5, m1, m2, precision, tol, _ptr(phi), _ptr(F),
+                                 ctypes.byref(S), info)
+        self._check(rc, "force")
+        return F, S.value, info
+
+    # -- device calls (torch tensors)
+    def field_bytes(self, precision):
+        return int(self.lib.eofa_field_bytes(self.ctx, precision))
+
+    def hop_dev(self, precision, out_parity, dagger, inp, out):
+        self._check(self.lib.eofa_hop_dev(self.ctx, precision, out_parity, int(dagger), _ptr(inp), _ptr(out),
+                                          _stream()), "hop_dev")
+
+    def pack_dev(self, precision, canon, even, odd):
+        self._check(self.lib.eofa_pack_dev(self.ctx, precision, _ptr(canon), _ptr(even), _ptr(odd), _stream()),
+                    "pack_dev")
+
+    def unpack_dev(self, precision, even, odd, canon):
+        self._check(self.lib.eofa_unpack_dev(self.ctx, precision, _ptr(even), _ptr(odd), _ptr(canon), _stream()),
+                    "unpack_dev")
+
+    def dwf_apply_dev(self, psi, out, alpha, M5, mf, dagger=False):
+        self._check(self.lib.eofa_dwf_apply_dev(self.ctx, self.Ls, alpha, M5, mf, int(dagger), _ptr(psi), _ptr(out),
+                                                _stream()), "dwf_apply_dev")
+
+    def solve_dev(self, b, x, use_x0=False, **kw):
+        p = self.solve_params(use_x0=use_x0, **kw)
+        info = SolveInfo()
+        rc = self.lib.eofa_solve_dev(self.ctx, ctypes.byref(p), _ptr(b), _ptr(x), ctypes.byref(info), _stream())
+        self._check(rc, "solve_dev")
+        return info
+
+    def action_dev(self, phi, alpha, M5, m1, m2, precision=PREC_F64, tol=1e-10):
+        S = ctypes.c_double()
+        info = (SolveInfo * 2)()
+        rc = self.lib.eofa_action_dev(self.ctx, self.Ls, alpha, M5, m1, m2, precision, tol, _ptr(phi),
+                                      ctypes.byref(S), info, _stream())
+        self._check(rc, "action_dev")
+        return S.value, info
+
+    def force_dev(self, phi, F, alpha, M5, m1, m2, precision=PREC_F64, tol=1e-10):
+        S = ctypes.c_double()
+        info = (SolveInfo * 2)()
+        rc = self.lib.eofa_force_dev(self.ctx, self.Ls, alpha, M5, m1, m2, precision, tol, _ptr(phi), _ptr(F),
+                                     ctypes.byref(S), info, _stream())
+        self._check(rc, "force_dev")
+        return S.value, info
+
+    def force_from_chi_dev(self, k, chiL, chiR, F):
+        self._check(self.lib.eofa_force_from_chi_dev(self.ctx, k, _ptr(chiL), _ptr(chiR), _ptr(F), _stream()),
+                    "force_from_chi_dev")
+
+    def grad_from_chi_dev(self, k, chiL, chiR, G):
+        self._check(self.lib.eofa_grad_from_chi_dev(self.ctx, k, _ptr(chiL), _ptr(chiR), _ptr(G), _stream()),
+                    "grad_from_chi_dev")
+
+    def link_update_dev(self, eps, P, U=None):
+        self._check(self.lib.eofa_link_update_dev(self.ctx, eps, _ptr(P), _ptr(U) if U is not None else None,
+                                                  _stream()), "link_update_dev")
+
+
+def solve_batched(lattices, params, bs, xs):
+    """Solve len(lattices) systems; params: list of SolveParams; bs, xs: numpy arrays."""
+    lib = load_library()
+    n = len(lattices)
+    ctxs = (ctypes.c_void_p * n)(*[lat.ctx.value for lat in lattices])
+    prm = (SolveParams * n)(*params)
+    bp = (ctypes.c_void_p * n)(*[_ptr(b) for b in bs])
+    xp = (ctypes.c_void_p * n)(*[_ptr(x) for x in xs])
+    info = (SolveInfo * n)()
+    rc = lib.eofa_solve_batched(ctxs, n, prm, bp, xp, info)
+    if rc not in (OK,):
+        raise EOFAError(rc, "solve_batched")
+    return info

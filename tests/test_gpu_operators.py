@@ -1,0 +1,125 @@
+"""GPU parity of the operator kernels against the FP64 oracle (through the C ABI).
+
+Tolerance: 1e-12 relative L2 per output vector for FP64 operator applications.
+"""
+import numpy as np
+import pytest
+
+from oracle import dwf
+from paper_1611_00298_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+CASES = [
+    # dims, Ls, alpha, M5, mf, bc
+    ((4, 4, 4, 4), 8, 2.0, 1.8, 0.04, -1),
+    ((2, 2, 2, 2), 4, 2.0, 1.8, 0.04, -1),    # L = 2: x+mu = x-mu
+    ((4, 2, 6, 4), 5, 1.0, 1.8, 0.3, +1),     # Shamir, odd Ls, periodic
+    ((2, 4, 2, 6), 1, 3.0, 1.4, 0.0, -1),     # Ls = 1, m_f = 0
+    ((4, 4, 2, 2), 6, 4.0, 1.8, 1.0, -1),     # m_f = 1
+    ((6, 4, 4, 8), 12, 2.0, 1.8, 0.0362, -1),  # several tiles, ragged tail
+]
+
+
+@pytest.fixture(scope="module")
+def eofa():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1611_00298_gb300 import eofa as e
+    e.load_library()
+    return e
+
+
+def _setup(eofa, dims, Ls, bc, seed=1, eps=0.5):
+    U = inputs.gauge_field(dims, eps, seed)
+    lat = eofa.Lattice(dims, Ls, bc_t=bc)
+    lat.gauge_load(U)
+    return lat, U
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_dwf_apply_parity(eofa, case):
+    dims, Ls, alpha, M5, mf, bc = case
+    lat, U = _setup(eofa, dims, Ls, bc)
+    psi = inputs.fermion5d(dims, Ls, 2)
+    out = lat.dwf_apply(psi, alpha, M5, mf)
+    assert _rel(out, dwf.dwf(U, psi, alpha, M5, mf, bc)) < 1e-12
+    out = lat.dwf_apply(psi, alpha, M5, mf, dagger=True)
+    assert _rel(out, dwf.dwf_dag(U, psi, alpha, M5, mf, bc)) < 1e-12
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_eofa_apply_parity(eofa, case):
+    dims, Ls, alpha, M5, mf, bc = case
+    lat, U = _setup(eofa, dims, Ls, bc)
+    psi = inputs.fermion5d(dims, Ls, 3)
+    out = lat.eofa_apply(psi, alpha, M5, mf)
+    assert _rel(out, dwf.deofa(U, psi, alpha, M5, mf, bc)) < 1e-12
+
+
+def test_gauge_load_rejects_non_unitary(eofa):
+    dims = (2, 2, 2, 2)
+    U = inputs.gauge_field(dims, 0.5, 1)
+    U[0, 0, 0, 1, 2] *= 1.001
+    lat = eofa.Lattice(dims, 4)
+    with pytest.raises(eofa.EOFAError) as ei:
+        lat.gauge_load(U)
+    assert ei.value.code == eofa.EINVAL
+    U[0, 0, 0, 1, 2] = np.nan
+    with pytest.raises(eofa.EOFAError):
+        lat.gauge_load(U)
+
+
+def test_bad_arguments(eofa):
+    with pytest.raises(eofa.EOFAError):
+        eofa.Lattice((3, 4, 4, 4), 8)
+    with pytest.raises(eofa.EOFAError):
+        eofa.Lattice((4, 4, 4, 4), 0)
+    lat = eofa.Lattice((2, 2, 2, 2), 4)
+    with pytest.raises(eofa.EOFAError):  # no gauge loaded
+        lat.dwf_apply(np.zeros(lat.shape5, complex), 2.0, 1.8, 0.1)
+    lat.gauge_load(inputs.gauge_field((2, 2, 2, 2), 0.3, 1))
+    p = lat.solve_params(system=eofa.SYS_EOFA_L, m1=0.5, m2=0.2)
+    with pytest.raises(eofa.EOFAError):
+        lat.solve(np.ones(lat.shape5, complex), system=eofa.SYS_EOFA_L, m1=0.5, m2=0.2)
+    del p
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-13), (1, 2e-6), (2, 2e-3)])
+@pytest.mark.parametrize("case", [CASES[0], CASES[1], CASES[5]])
+def test_hop_kernel_each_precision(eofa, case, prec, tol):
+    """Even-odd hop in FP64 / FP32 / FP16 storage against the oracle hop."""
+    import torch
+    dims, Ls, alpha, M5, mf, bc = case
+    lat, U = _setup(eofa, dims, Ls, bc)
+    psi = inputs.fermion5d(dims, Ls, 4)
+    X, Y, Z, T = dims
+    t, z, y, x = np.meshgrid(*[np.arange(n) for n in (T, Z, Y, X)], indexing="ij")
+    par = (x + y + z + t) % 2
+    for out_par in (0, 1):
+        for dag in (0, 1):
+            src = psi * (par == 1 - out_par)[None, :, :, :, :, None, None]
+            ref = dwf.wilson_hop(U, src, bc, dagger=bool(dag)) * (par == out_par)[None, :, :, :, :, None, None]
+            dev = torch.from_numpy(src.copy()).cuda()
+            nb = lat.field_bytes(prec)
+            ev = torch.empty(nb, dtype=torch.uint8, device="cuda")
+            od = torch.empty(nb, dtype=torch.uint8, device="cuda")
+            oe = torch.zeros(nb, dtype=torch.uint8, device="cuda")
+            oo = torch.zeros(nb, dtype=torch.uint8, device="cuda")
+            lat.pack_dev(prec, dev, ev, od)
+            if out_par == 0:
+                lat.hop_dev(prec, 0, dag, od, oe)
+                lat.pack_dev(prec, torch.zeros_like(dev), ev, oo)
+            else:
+                lat.hop_dev(prec, 1, dag, ev, oo)
+                lat.pack_dev(prec, torch.zeros_like(dev), oe, od)
+            res = torch.empty_like(dev)
+            lat.unpack_dev(prec, oe, oo, res)
+            torch.cuda.synchronize()
+            got = res.cpu().numpy()
+            assert _rel(got, ref) < tol, (out_par, dag, _rel(got, ref))

@@ -1,0 +1,113 @@
+"""GPU solves, EOFA action and force against the FP64 oracle (through the C ABI).
+
+Solves are judged by the FP64 true residual of the full system (<= tol) on
+both sides; solutions are compared at a tolerance set by the residuals.
+"""
+import numpy as np
+import pytest
+
+from oracle import dwf, eofa as oeofa, solve as osolve
+from paper_1611_00298_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+ALPHA, M5, M1, M2 = 2.0, 1.8, 0.04, 1.0
+
+
+@pytest.fixture(scope="module")
+def eofa():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1611_00298_gb300 import eofa as e
+    e.load_library()
+    return e
+
+
+def _setup(eofa, dims, Ls, bc=-1, seed=1, eps=0.3):
+    U = inputs.gauge_field(dims, eps, seed)
+    lat = eofa.Lattice(dims, Ls, bc_t=bc)
+    lat.gauge_load(U)
+    return lat, U
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2])
+@pytest.mark.parametrize("alpha", [1.0, 2.0])
+def test_dwf_solve_true_residual(eofa, prec, alpha):
+    dims, Ls = (4, 4, 4, 4), 8
+    lat, U = _setup(eofa, dims, Ls)
+    b = inputs.fermion5d(dims, Ls, 5)
+    x, info = lat.solve(b, system=eofa.SYS_DWF, alpha=alpha, M5=M5, mf=M1, precision=prec, tol=1e-10)
+    res = np.linalg.norm(b - dwf.dwf(U, x, alpha, M5, M1, -1)) / np.linalg.norm(b)
+    assert res <= 1.05e-10, res
+    assert info.true_resid <= 1e-10
+    assert abs(info.true_resid - res) < 1e-3 * res + 1e-14
+    if prec > 0:
+        assert info.reliable_updates >= 1
+
+
+def test_dwf_solve_matches_oracle_solution(eofa):
+    dims, Ls = (4, 4, 2, 4), 6
+    lat, U = _setup(eofa, dims, Ls, eps=0.5)
+    b = inputs.fermion5d(dims, Ls, 6)
+    x, info = lat.solve(b, system=eofa.SYS_DWF, alpha=ALPHA, M5=M5, mf=0.1, tol=1e-13)
+    xo, it, res = osolve.cgnr(lambda v: dwf.dwf(U, v, ALPHA, M5, 0.1, -1),
+                              lambda v: dwf.dwf_dag(U, v, ALPHA, M5, 0.1, -1), b, tol=1e-13)
+    assert _rel(x, xo) < 1e-10
+
+
+def test_dwf_solve_warm_start(eofa):
+    dims, Ls = (4, 4, 4, 4), 8
+    lat, U = _setup(eofa, dims, Ls)
+    b = inputs.fermion5d(dims, Ls, 7)
+    x, info = lat.solve(b, system=eofa.SYS_DWF, alpha=ALPHA, M5=M5, mf=M1, tol=1e-8)
+    x2, info2 = lat.solve(b, x0=x, system=eofa.SYS_DWF, alpha=ALPHA, M5=M5, mf=M1, tol=1e-10)
+    assert info2.true_resid <= 1e-10
+    assert info2.iters < info.iters
+
+
+@pytest.mark.parametrize("which,shift", [(1, 0.0), (2, -1.0), (1, -0.3), (2, -0.7)])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_eofa_system_solve(eofa, which, shift, prec):
+    """Eq. (8): (H(m) + a Delta P) psi = phi; residual checked with the oracle operator."""
+    dims, Ls = (4, 4, 4, 4), 8
+    lat, U = _setup(eofa, dims, Ls, eps=0.4)
+    rhs = inputs.fermion5d(dims, Ls, 8)
+    x, info = lat.solve(rhs, system=which, alpha=ALPHA, M5=M5, m1=M1, m2=M2, shift=shift, precision=prec, tol=1e-10)
+    wh = "L" if which == 1 else "R"
+    Ax = oeofa.system_apply(U, x, ALPHA, M5, M1, M2, wh, shift, -1)
+    res = np.linalg.norm(rhs - Ax) / np.linalg.norm(rhs)
+    assert res <= 1.05e-10, res
+
+
+def test_action_matches_oracle(eofa):
+    dims, Ls = (4, 4, 4, 4), 8
+    lat, U = _setup(eofa, dims, Ls)
+    phi = inputs.fermion4d(dims, 1)
+    S_ref = oeofa.action(U, phi, Ls, ALPHA, M5, M1, M2, -1, tol=1e-13)
+    for prec in (0, 1, 2):
+        S, info = lat.action(phi, ALPHA, M5, M1, M2, precision=prec, tol=1e-11)
+        assert abs(S - S_ref) < 1e-9 * abs(S_ref), (prec, S, S_ref)
+
+
+@pytest.mark.parametrize("alpha", [1.0, 2.0])
+def test_force_matches_oracle(eofa, alpha):
+    import torch
+    dims, Ls = (4, 2, 2, 4), 6
+    lat, U = _setup(eofa, dims, Ls, eps=0.6)
+    phi = inputs.fermion4d(dims, 2)
+    F, S, info = lat.force(phi, alpha, M5, M1, M2, precision=0, tol=1e-13)
+    Fo = oeofa.force(U, phi, Ls, alpha, M5, M1, M2, -1, tol=1e-13)
+    assert np.abs(F - Fo).max() < 1e-9 * np.abs(Fo).max()
+    # force kernel alone, same chi on both sides: 1e-12
+    chiL, chiR, _ = oeofa.pseudofermion_solutions(U, phi, Ls, alpha, M5, M1, M2, -1, tol=1e-12)
+    k = oeofa.k_coefficient(Ls, alpha, M1, M2)
+    Fo2, _ = oeofa.force_from_chi(U, chiL, chiR, k, -1)
+    Fd = torch.empty(lat.shapeU, dtype=torch.complex128, device="cuda")
+    lat.force_from_chi_dev(k, torch.from_numpy(chiL).cuda(), torch.from_numpy(chiR).cuda(), Fd)
+    torch.cuda.synchronize()
+    assert _rel(Fd.cpu().numpy(), Fo2) < 1e-12
