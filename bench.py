@@ -1,0 +1,386 @@
+#!/usr/bin/env python
+"""Benchmark of the EOFA hot path on GB300.
+
+Workload: the paper-shaped lattice 24^3 x 64, Ls = 24 (the 24ID volume of
+Table 1), Moebius alpha = 2 (c = 1, d = 1/2), M5 = 1.8, synthetic
+strange-like mass pair m1 = 0.0362, m2 = 1.0, seeded synthetic SU(3) links
+exp(i 0.7 sum_a h_a lambda_a) (seed 3) and a Gaussian pseudofermion.
+
+One step = one EOFA pseudofermion force evaluation (Sec. 3.3, Eq. (7)),
+the operation that dominates an EOFA trajectory (Table 4): the two
+Cayley / even-odd preconditioned solves of Eq. (8) for chi_L and chi_R in
+mixed precision (FP32 inner CG, FP64 reliable updates) to a true residual of
+1e-10, the action value of Eq. (5) and the force kernel.
+
+value = whole-job dslash bandwidth: algorithmic bytes of every even-odd
+dslash (hop) launched in the timed steps, summed over ranks, divided by the
+slowest rank's time.  The roofline object reports the hop kernel itself
+(average duration from CUDA events recorded around each launch on its
+stream during the timed steps).  "solve" compares the same chi_L solve in
+mixed precision and in plain FP64 on the GPU.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "DWF dslash GB/s (% HBM roofline); EOFA solve time mixed vs FP64 at 1e-10"
+WORKLOAD = dict(dims=(24, 24, 24, 64), Ls=24, alpha=2.0, M5=1.8, m1=0.0362, m2=1.0, eps=0.7, seed=3, bc=-1)
+SMALL = dict(dims=(8, 8, 8, 8), Ls=8, alpha=2.0, M5=1.8, m1=0.0362, m2=1.0, eps=0.7, seed=3, bc=-1)
+FALLBACK_HBM_GBS = 6800.0
+
+
+def hop_bytes_per_site(prec: int, Ls: int) -> float:
+    """Algorithmic bytes per output 5D site of one even-odd hop: one input and one
+    output spinor plus 8 links amortised over Ls (FP16: FP32 per-site scale, FP32 links)."""
+    if prec == 0:
+        return 192 + 192 + 8 * 144 / Ls
+    if prec == 1:
+        return 96 + 96 + 8 * 72 / Ls
+    return (48 + 4) + (48 + 4) + 8 * 72 / Ls
+
+
+def hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            d = json.load(open(path))
+            for key in ("hbm_gbs", "hbm_GBs", "hbm"):
+                if key in d:
+                    v = d[key]
+                    return float(v["burst"] if isinstance(v, dict) and "burst" in v else v), "measured"
+        except Exception:
+            pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                       "-lms", "200", "-i", str(gpu_index)], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        rows = [ln.strip().split(", ") for ln in open(self.f.name) if ln.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+                for k, nm in enumerate(names):
+                    if r[5 + k].strip().lower() == "active":
+                        reasons.add(nm)
+            except Exception:
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(U, wl, budget_s=20.0):
+    """The FP64 oracle's Wilson dslash on a bounded sample of the workload (host cores)."""
+    import numpy as np
+
+    from oracle import dwf
+    from paper_1611_00298_gb300 import inputs
+
+    X, Y, Z, T = wl["dims"]
+    ns = 2  # s-slices in the sample
+    psi = inputs.fermion5d(wl["dims"], ns, wl["seed"], stream=9)
+    t0 = time.perf_counter()
+    reps = 0
+    while True:
+        dwf.wilson(U, psi, wl["M5"], wl["bc"])
+        reps += 1
+        if time.perf_counter() - t0 > budget_s / 2 or reps >= 3:
+            break
+    dt = (time.perf_counter() - t0) / reps
+    sites = ns * X * Y * Z * T
+    gbs = sites * hop_bytes_per_site(0, wl["Ls"]) / dt / 1e9
+    del np
+    return {"value": round(gbs, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": f"numpy FP64 D_w (both parities) on {ns} of {wl['Ls']} s-slices of {X}x{Y}x{Z}x{T}, "
+                      f"{reps} reps, {dt:.2f} s each; bytes counted as for the FP64 hop at Ls={wl['Ls']}"}
+
+
+def run_reference(args, wl, rank):
+    if rank != 0:
+        return 0
+    from paper_1611_00298_gb300 import inputs
+    U = inputs.gauge_field(wl["dims"], wl["eps"], wl["seed"])
+    vals = []
+    cb = None
+    for i in range(args.warmup + args.steps):
+        cb = cpu_baseline(U, wl, budget_s=10.0)
+        if i >= args.warmup:
+            vals.append(cb["value"])
+    v = statistics.mean(vals)
+    cb["value"] = round(v, 4)
+    line = {"impl": "reference", "metric": METRIC, "value": round(v, 4), "unit": "GB/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(wl, "oracle FP64 Wilson dslash sample"),
+            "cpu_baseline": cb, "e2e": {"value": round(v, 4), "unit": "GB/s", "h2d_bytes_per_step": 0,
+                                        "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def hop_only(args, wl):
+    """Launch the even-odd hop alone on a random field (profiling target)."""
+    import torch
+
+    from paper_1611_00298_gb300 import build, eofa, inputs
+    if not os.path.exists(eofa.LIB_PATH):
+        build.build()
+    prec = {"f32": 1, "f16": 2}[args.precision]
+    U = inputs.gauge_field(wl["dims"], wl["eps"], wl["seed"])
+    lat = eofa.Lattice(wl["dims"], wl["Ls"], bc_t=wl["bc"])
+    lat.gauge_load(U)
+    canon = torch.randn(lat.V * wl["Ls"] * 24, dtype=torch.float64, device="cuda")
+    nb = lat.field_bytes(prec)
+    e = torch.empty(nb, dtype=torch.uint8, device="cuda")
+    o = torch.empty_like(e)
+    out = torch.empty_like(e)
+    lat.pack_dev(prec, canon, e, o)
+    del canon
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for _ in range(args.hop_reps):
+        lat.hop_dev(prec, 0, 0, o, out)
+    ev1.record()
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / args.hop_reps
+    n5h = lat.V // 2 * wl["Ls"]
+    gbs = hop_bytes_per_site(prec, wl["Ls"]) * n5h / (ms / 1000) / 1e9
+    print(json.dumps({"hop_only": True, "dims": wl["dims"], "Ls": wl["Ls"], "precision": args.precision,
+                      "avg_ms": round(ms, 4), "GBs": round(gbs, 1), "kernel_version": kernel_version()}))
+    lat.close()
+    return 0
+
+
+def workload_config(wl, what):
+    X, Y, Z, T = wl["dims"]
+    return {"workload": f"EOFA force evaluation, {X}^3x{T} Ls={wl['Ls']} Moebius alpha={wl['alpha']} "
+                        f"M5={wl['M5']} m1={wl['m1']} m2={wl['m2']}, synthetic links eps={wl['eps']} seed {wl['seed']}",
+            "lattice": f"{X}x{Y}x{Z}x{T}", "Ls": wl["Ls"], "what": what, "global_batch": 1,
+            "l2": "inputs larger than L2 (each FP32 half-checkerboard field is 1.02 GB)",
+            "parallelism": "replicas (one independent lattice per GPU)"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="f32", choices=["f32", "f16"])
+    ap.add_argument("--small", action="store_true", help="8^4 x 8 lattice (quick check)")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 solve comparison")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--hop-only", action="store_true",
+                    help="only launch the even-odd hop kernel (for ncu captures); see --dims, --hop-reps")
+    ap.add_argument("--dims", default=None, help="X,Y,Z,T override for --hop-only")
+    ap.add_argument("--hop-reps", type=int, default=4)
+    args = ap.parse_args()
+    wl = dict(SMALL if args.small else WORKLOAD)
+    if args.dims:
+        wl["dims"] = tuple(int(v) for v in args.dims.split(","))
+    if args.hop_only:
+        return hop_only(args, wl)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, wl, rank)
+
+    import numpy as np
+    import torch
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+
+    from paper_1611_00298_gb300 import build, eofa, inputs
+    if not os.path.exists(eofa.LIB_PATH):
+        build.build()
+    eofa.load_library()
+
+    prec = eofa.PREC_MIXED_F32 if args.precision == "f32" else eofa.PREC_MIXED_F16
+    Ls = wl["Ls"]
+    U = inputs.gauge_field(wl["dims"], wl["eps"], wl["seed"] + 100 * rank)
+    phi_np = inputs.fermion4d(wl["dims"], wl["seed"] + 100 * rank)
+    lat = eofa.Lattice(wl["dims"], Ls, bc_t=wl["bc"])
+    lat.gauge_load(U)
+    phi = torch.from_numpy(phi_np).cuda()
+    F = torch.empty(lat.shapeU, dtype=torch.complex128, device="cuda")
+    kw = dict(alpha=wl["alpha"], M5=wl["M5"], m1=wl["m1"], m2=wl["m2"], precision=prec, tol=1e-10)
+    n5h = lat.V // 2 * Ls
+
+    def step():
+        S, info = lat.force_dev(phi, F, **kw)
+        return S, [info[0].as_dict(), info[1].as_dict()]
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    clocks = ClockSampler(local_rank)
+    l0 = eofa.kernel_launches()
+    lat.profile_start()
+    barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    infos, actions = [], []
+    for _ in range(args.steps):
+        S, inf = step()
+        infos.append(inf)
+        actions.append(S)
+    ev1.record()
+    torch.cuda.synchronize()
+    barrier()
+    elapsed = ev0.elapsed_time(ev1) / 1000.0
+    launches = eofa.kernel_launches() - l0
+    hop_launches, kind_ms = lat.profile_stop()
+    clk = clocks.stop()
+
+    bytes_per_hop = [hop_bytes_per_site(p, Ls) * n5h for p in range(3)]
+    hop_bytes = sum(hop_launches[p] * bytes_per_hop[p] for p in range(3))
+    t_max = elapsed
+    total_bytes = hop_bytes
+    if dist is not None:
+        t = torch.tensor([elapsed], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+        b = torch.tensor([hop_bytes], device="cuda", dtype=torch.float64)
+        dist.all_reduce(b)
+        total_bytes = float(b.item())
+    value = total_bytes / t_max / 1e9
+
+    inner = 1 if prec == eofa.PREC_MIXED_F32 else 2
+    avg_ms = kind_ms[inner] / max(1, hop_launches[inner])
+    achieved = bytes_per_hop[inner] / (avg_ms / 1000.0) / 1e9
+    peak, peak_src = hbm_peak()
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "hop_traffic.json")
+    if os.path.exists(tpath):
+        try:
+            td = json.load(open(tpath))
+            key = f"{'fp32' if inner == 1 else 'fp16'}_24x24x24x64_Ls24"
+            if key in td and td[key].get("kernel_version") == kernel_version():
+                traffic = td[key]["bytes_per_launch"]
+        except Exception:
+            traffic = None
+
+    result = None
+    if rank == 0:
+        # end to end through the public host API: pinned host phi in, host F out
+        phi_h = torch.from_numpy(phi_np.copy()).pin_memory()
+        F_h = torch.empty(lat.shapeU, dtype=torch.complex128).pin_memory()
+        lat.profile_start()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            lat.force(phi_h.numpy(), alpha=wl["alpha"], M5=wl["M5"], m1=wl["m1"], m2=wl["m2"], precision=prec,
+                      tol=1e-10, out=F_h.numpy())
+        torch.cuda.synchronize()
+        e2e_t = (time.perf_counter() - t0) / args.steps
+        hl2, _ = lat.profile_stop()
+        e2e_bytes = sum(hl2[p] * bytes_per_hop[p] for p in range(3)) / args.steps
+        e2e = {"value": round(e2e_bytes / e2e_t / 1e9, 2), "unit": "GB/s",
+               "h2d_bytes_per_step": int(phi_np.nbytes), "d2h_bytes_per_step": int(F_h.numel() * 16 + 8),
+               "seconds_per_step": round(e2e_t, 4)}
+
+        mixed_s = statistics.mean(i[0]["seconds"] for i in infos)
+        solve = {"system": "chi_L = H(m1)^-1 Omega_- P_- phi (Eq. (8), a = 0)",
+                 "mixed_f32_seconds": round(mixed_s, 4),
+                 "mixed_iters": infos[-1][0]["iters"], "mixed_reliable_updates": infos[-1][0]["reliable_updates"],
+                 "mixed_true_resid": infos[-1][0]["true_resid"]}
+        if not args.no_fp64:
+            b = torch.empty(lat.V * Ls * 12, dtype=torch.complex128, device="cuda")
+            x = torch.zeros_like(b)
+            # same right-hand side as chi_L: Omega_- P_- phi
+            k, Op, Om = eofa.coefficients(Ls, wl["alpha"], wl["m1"], wl["m2"])
+            bm = np.zeros(lat.shape5, dtype=np.complex128)
+            bm[..., 2:, :] = Om[:, None, None, None, None, None, None] * phi_np[None, ..., 2:, :]
+            b.copy_(torch.from_numpy(bm.reshape(-1)))
+            info64 = lat.solve_dev(b, x, system=eofa.SYS_EOFA_L, alpha=wl["alpha"], M5=wl["M5"], m1=wl["m1"],
+                                   m2=wl["m2"], shift=0.0, precision=eofa.PREC_F64, tol=1e-10)
+            solve.update({"fp64_seconds": round(info64.seconds, 4), "fp64_iters": info64.iters,
+                          "fp64_true_resid": info64.true_resid,
+                          "fp64_over_mixed": round(info64.seconds / mixed_s, 3)})
+        hop_share = kind_ms[inner] / 1000.0 / elapsed
+        roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                    "frac": round(achieved / peak, 4), "traffic": traffic,
+                    "kernel": f"even-odd hop, {'FP32' if inner == 1 else 'FP16'} storage, all Ls slices",
+                    "bytes_per_launch": int(bytes_per_hop[inner]), "avg_launch_ms": round(avg_ms, 4),
+                    "launches_timed": hop_launches[inner], "share_of_step": round(hop_share, 4),
+                    "peak_source": f"{peak_src} ({'of measured' if peak_src == 'measured' else 'of fallback'})"}
+        result = {
+            "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(1000 * t_max / args.steps, 2), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+            "data": "synthetic (seeded SU(3) links and Gaussian pseudofermion; no ensemble)",
+            "config": workload_config(wl, f"mixed {args.precision.upper()} inner CG, FP64 reliable updates"),
+            "roofline": roofline, "e2e": e2e, "solve": solve, "clocks": clk, "gpu_launches": int(launches),
+            "hop_launches_by_precision": {"fp64": hop_launches[0], "fp32": hop_launches[1], "fp16": hop_launches[2]},
+            "action": actions[-1],
+        }
+        if not args.no_cpu:
+            result["cpu_baseline"] = cpu_baseline(U, wl)
+        print(json.dumps(result), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    lat.close()
+    return 0
+
+
+def kernel_version():
+    """Hash of the hop kernel source, to invalidate stored ncu traffic when it changes."""
+    import hashlib
+    src = open(os.path.join(ROOT, "paper_1611_00298_gb300", "csrc", "hop.cu"), "rb").read()
+    return hashlib.sha256(src).hexdigest()[:16]
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -183,6 +183,21 @@ int eofa_link_update_dev(eofa_ctx* ctx, double eps, const double* P_dev, double*
 int eofa_solve_batched(eofa_ctx* const* ctxs, int n, const eofa_solve_params* params,
                        const double* const* b, double* const* x, eofa_solve_info* info);
 
+/* Instrumentation.  eofa_kernel_launches: number of CUDA kernels this
+ * library has launched since it was loaded (all contexts).
+ * eofa_profile_start / _stop: while on, every even-odd hop and 5D-local
+ * kernel launch on the context is bracketed by CUDA events recorded on its
+ * stream (at most 65536 launches); _stop waits for them and returns per-kind
+ * launch counts and summed milliseconds.  Kinds: 0..2 hop in
+ * FP64 / FP32 / FP16 storage, 3..5 5D-local kernel in the same order. */
+typedef struct {
+    long long launches[6];
+    double ms[6];
+} eofa_profile;
+long long eofa_kernel_launches(void);
+int eofa_profile_start(eofa_ctx* ctx);
+int eofa_profile_stop(eofa_ctx* ctx, eofa_profile* out);
+
 #ifdef __cplusplus
 }
 #endif

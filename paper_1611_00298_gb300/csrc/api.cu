@@ -158,6 +158,7 @@ int eofa_create(eofa_ctx** out, const int dims[4], int Ls, int bc_t, int flags) 
     ctx->canon5 = ctx->canon5b = nullptr;
     ctx->coef = ctx->red = ctx->red_host = nullptr;
     ctx->stream = nullptr;
+    ctx->prof = nullptr;
     try {
         EOFA_CUDA(cudaGetDevice(&ctx->device));
         EOFA_CUDA(cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, ctx->device));
@@ -188,6 +189,10 @@ int eofa_destroy(eofa_ctx* ctx) {
     for (auto& kv : ctx->bufs) cudaFree(kv.second);
     if (ctx->red_host) cudaFreeHost(ctx->red_host);
     if (ctx->stream) cudaStreamDestroy(ctx->stream);
+    if (ctx->prof) {
+        for (auto& e : ctx->prof->ev) cudaEventDestroy(e);
+        delete ctx->prof;
+    }
     delete ctx;
     return EOFA_OK;
 }

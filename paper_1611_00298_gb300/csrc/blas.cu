@@ -135,7 +135,7 @@ void blas_axpby(const eofa_ctx* ctx, int prec, double a, const void* x, double b
     if (prec == P64) axpby_kernel<P64, P64><<<nb, 256, 0, st>>>(g, a, x, b, y);
     else if (prec == P32) axpby_kernel<P32, P32><<<nb, 256, 0, st>>>(g, a, x, b, y);
     else axpby_kernel<P16, P16><<<nb, 256, 0, st>>>(g, a, x, b, y);
-    EOFA_CUDA(cudaGetLastError());
+    EOFA_LAUNCHED();
 }
 
 void blas_copy(const eofa_ctx* ctx, int po, void* out, int pi, const void* in, cudaStream_t st) {
@@ -144,7 +144,7 @@ void blas_copy(const eofa_ctx* ctx, int po, void* out, int pi, const void* in, c
 #define CP(A, B) if (po == A && pi == B) { axpby_kernel<A, B><<<nb, 256, 0, st>>>(g, 1.0, in, 0.0, out); }
     CP(P64, P64) CP(P64, P32) CP(P64, P16) CP(P32, P64) CP(P32, P32) CP(P32, P16) CP(P16, P64) CP(P16, P32) CP(P16, P16)
 #undef CP
-    EOFA_CUDA(cudaGetLastError());
+    EOFA_LAUNCHED();
 }
 
 void blas_zero(const eofa_ctx* ctx, int prec, void* x, cudaStream_t st) {
@@ -156,7 +156,7 @@ void blas_norm2(const eofa_ctx* ctx, int prec, const void* x, int slot, cudaStre
     if (prec == P64) norm2_kernel<P64><<<RED_BLOCKS, RED_THREADS, 0, st>>>(g, x, ctx->red, slot);
     else if (prec == P32) norm2_kernel<P32><<<RED_BLOCKS, RED_THREADS, 0, st>>>(g, x, ctx->red, slot);
     else norm2_kernel<P16><<<RED_BLOCKS, RED_THREADS, 0, st>>>(g, x, ctx->red, slot);
-    EOFA_CUDA(cudaGetLastError());
+    EOFA_LAUNCHED();
 }
 
 void blas_dot(const eofa_ctx* ctx, int prec, const void* x, const void* y, int slot, cudaStream_t st) {
@@ -164,7 +164,7 @@ void blas_dot(const eofa_ctx* ctx, int prec, const void* x, const void* y, int s
     if (prec == P64) dot_kernel<P64><<<RED_BLOCKS, RED_THREADS, 0, st>>>(g, x, y, ctx->red, slot);
     else if (prec == P32) dot_kernel<P32><<<RED_BLOCKS, RED_THREADS, 0, st>>>(g, x, y, ctx->red, slot);
     else dot_kernel<P16><<<RED_BLOCKS, RED_THREADS, 0, st>>>(g, x, y, ctx->red, slot);
-    EOFA_CUDA(cudaGetLastError());
+    EOFA_LAUNCHED();
 }
 
 double red_fetch(const eofa_ctx* ctx, int slot, cudaStream_t st) {
@@ -233,10 +233,10 @@ void blas_cg_update(const eofa_ctx* ctx, int prec, int prec_x, double alpha, con
 #define CGU(A, B) if (prec == A && prec_x == B) cg_update_kernel<A, B><<<RED_BLOCKS, RED_THREADS, 0, st>>>(g, alpha, p, q, x, r, ctx->red, slot);
     CGU(P64, P64) CGU(P32, P32) CGU(P16, P32) CGU(P16, P16)
 #undef CGU
-    EOFA_CUDA(cudaGetLastError());
+    EOFA_LAUNCHED();
 }
 
 void blas_flat_dot(const eofa_ctx* ctx, long long ncplx, const double* a, const double* b, int slot, cudaStream_t st) {
     flat_dot_kernel<<<RED_BLOCKS, RED_THREADS, 0, st>>>(ncplx, (const double2*)a, (const double2*)b, ctx->red, slot);
-    EOFA_CUDA(cudaGetLastError());
+    EOFA_LAUNCHED();
 }

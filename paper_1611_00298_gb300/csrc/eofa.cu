@@ -204,8 +204,9 @@ ChiBufs eofa_chis(eofa_ctx* ctx, int Ls, double alpha, double M5, double m1, dou
     EOFA_CUDA(cudaMemcpyAsync(om + EOFA_MAX_LS, Om.data(), Ls * sizeof(double), cudaMemcpyHostToDevice, st));
     long long n = V * 12 * Ls;
     embed_kernel<<<nblk(n, 256), 256, 0, st>>>(V, Ls, (const double2*)phi_dev, om + EOFA_MAX_LS, -1, (double2*)c.bL);
+    EOFA_LAUNCHED();
     embed_kernel<<<nblk(n, 256), 256, 0, st>>>(V, Ls, (const double2*)phi_dev, om, +1, (double2*)c.bR);
-    EOFA_CUDA(cudaGetLastError());
+    EOFA_LAUNCHED();
     eofa_solve_params p;
     p.Ls = Ls;
     p.alpha = alpha;
@@ -276,7 +277,7 @@ static void launch_force(eofa_ctx* ctx, double k, const double* chiL, const doub
     long long nl = 4LL * ctx->V;
     force_kernel<<<nblk(nl, 128), 128, 0, st>>>(d, ctx->Ls, ctx->bc_t, k, (const double2*)U, (const double2*)chiL,
                                                 (const double2*)chiR, (double2*)F, mode);
-    EOFA_CUDA(cudaGetLastError());
+    EOFA_LAUNCHED();
 }
 
 int eofa_force_from_chi_dev(eofa_ctx* ctx, double k, const double* chiL_dev, const double* chiR_dev, double* F_dev,
@@ -346,7 +347,7 @@ int eofa_link_update_dev(eofa_ctx* ctx, double eps, const double* P_dev, double*
         double* Uc = (double*)ctx_buffer(ctx, "U", 0);
         long long nl = 4LL * ctx->V;
         link_update_kernel<<<nblk(nl, 128), 128, 0, st>>>(nl, eps, (const double2*)P_dev, (double2*)Uc, (double2*)U_dev);
-        EOFA_CUDA(cudaGetLastError());
+        EOFA_LAUNCHED();
         launch_gauge_pack(ctx, Uc, st);
     } catch (const eofa_error& e) {
         return fail(ctx, e.code, e.msg);

@@ -137,6 +137,7 @@ void launch_hop(const eofa_ctx* ctx, int prec, int out_parity, int dagger, const
     long long n5 = (long long)g.Vh * g.Ls;
     unsigned nb = (unsigned)((n5 + 127) / 128);
     const void* gauge = ctx->gauge[prec == P64 ? P64 : P32];
+    prof_begin(ctx, prec, st);
 #define HOP_CASE(PP)                                                                             \
     if (dagger) hop_kernel<PP, 1><<<nb, 128, 0, st>>>(g, out_parity, in, out, gauge);            \
     else hop_kernel<PP, 0><<<nb, 128, 0, st>>>(g, out_parity, in, out, gauge);
@@ -144,5 +145,6 @@ void launch_hop(const eofa_ctx* ctx, int prec, int out_parity, int dagger, const
     else if (prec == P32) { HOP_CASE(P32) }
     else { HOP_CASE(P16) }
 #undef HOP_CASE
-    EOFA_CUDA(cudaGetLastError());
+    EOFA_LAUNCHED();
+    prof_end(ctx, st);
 }

@@ -87,6 +87,13 @@ struct Op5 {
     double a_out, b_in;  // out = a_out * op(x) + b_in * y
 };
 
+// Kernel launch accounting and optional per-kernel CUDA-event timing.
+struct Prof {
+    bool on = false;
+    int used = 0;
+    std::vector<cudaEvent_t> ev;  // pairs (start, stop)
+    std::vector<int> kind;        // 0..2 hop per precision, 3..5 op5 per precision
+};
 // ------------------------------------------------------------------ context
 
 struct eofa_ctx {
@@ -109,6 +116,7 @@ struct eofa_ctx {
     double* red_host;         // pinned host mirror of reduction results
     std::map<std::string, void*> bufs;  // named workspace fields
     std::map<std::string, size_t> buf_sizes;
+    Prof* prof;
 };
 
 // ------------------------------------------------------------------ helpers
@@ -121,11 +129,21 @@ struct eofa_ctx {
         }                                                                      \
     } while (0)
 
+extern long long g_launches;
+void prof_begin(const struct eofa_ctx* ctx, int kind, cudaStream_t st);
+void prof_end(const struct eofa_ctx* ctx, cudaStream_t st);
+
 struct eofa_error {
     int code;
     std::string msg;
     eofa_error(int c, const std::string& m) : code(c), msg(m) {}
 };
+
+#define EOFA_LAUNCHED()                                                         \
+    do {                                                                       \
+        __atomic_add_fetch(&g_launches, 1LL, __ATOMIC_RELAXED);                \
+        EOFA_CUDA(cudaGetLastError());                                         \
+    } while (0)
 
 void* ctx_buffer(eofa_ctx* ctx, const std::string& name, size_t bytes);
 Geom ctx_geom(const eofa_ctx* ctx);

@@ -114,7 +114,7 @@ void launch_pack(const eofa_ctx* ctx, int prec, const double* canon, void* even,
     if (prec == P64) pack_kernel<P64><<<blocks(n, 256), 256, 0, st>>>(g, ctx->V, canon, even, odd);
     else if (prec == P32) pack_kernel<P32><<<blocks(n, 256), 256, 0, st>>>(g, ctx->V, canon, even, odd);
     else pack_kernel<P16><<<blocks(n, 256), 256, 0, st>>>(g, ctx->V, canon, even, odd);
-    EOFA_CUDA(cudaGetLastError());
+    EOFA_LAUNCHED();
 }
 
 void launch_unpack(const eofa_ctx* ctx, int prec, const void* even, const void* odd, double* canon, cudaStream_t st) {
@@ -123,26 +123,26 @@ void launch_unpack(const eofa_ctx* ctx, int prec, const void* even, const void* 
     if (prec == P64) unpack_kernel<P64><<<blocks(n, 256), 256, 0, st>>>(g, ctx->V, even, odd, canon);
     else if (prec == P32) unpack_kernel<P32><<<blocks(n, 256), 256, 0, st>>>(g, ctx->V, even, odd, canon);
     else unpack_kernel<P16><<<blocks(n, 256), 256, 0, st>>>(g, ctx->V, even, odd, canon);
-    EOFA_CUDA(cudaGetLastError());
+    EOFA_LAUNCHED();
 }
 
 void launch_gauge_pack(const eofa_ctx* ctx, const double* canon, cudaStream_t st) {
     Geom g = ctx_geom(ctx);
     long long n = 8LL * g.Vh;
     gauge_pack_kernel<<<blocks(n, 256), 256, 0, st>>>(g, canon, (double2*)ctx->gauge[P64], (float2*)ctx->gauge[P32]);
-    EOFA_CUDA(cudaGetLastError());
+    EOFA_LAUNCHED();
 }
 
 void launch_unitarity(const eofa_ctx* ctx, const double* canon, double* out_max, cudaStream_t st) {
     long long nl = 4LL * ctx->V;
     EOFA_CUDA(cudaMemsetAsync(out_max, 0, sizeof(double), st));
     unitarity_kernel<<<blocks(nl, 256), 256, 0, st>>>(nl, canon, (unsigned long long*)out_max);
-    EOFA_CUDA(cudaGetLastError());
+    EOFA_LAUNCHED();
 }
 
 void launch_rs5(const eofa_ctx* ctx, const double* in, double* out, cudaStream_t st) {
     long long V12 = 12LL * ctx->V;
     long long n = V12 * ctx->Ls;
     rs5_kernel<<<blocks(n, 256), 256, 0, st>>>(V12, ctx->Ls, (const double2*)in, (double2*)out);
-    EOFA_CUDA(cudaGetLastError());
+    EOFA_LAUNCHED();
 }

@@ -29,7 +29,7 @@ EXPORTS = [
     "eofa_field_bytes", "eofa_hop_dev", "eofa_pack_dev", "eofa_unpack_dev",
     "eofa_solve", "eofa_solve_dev", "eofa_action", "eofa_action_dev", "eofa_force", "eofa_force_dev",
     "eofa_force_from_chi_dev", "eofa_grad_from_chi_dev", "eofa_coefficients", "eofa_link_update_dev",
-    "eofa_solve_batched",
+    "eofa_solve_batched", "eofa_kernel_launches", "eofa_profile_start", "eofa_profile_stop",
 ]
 
 
@@ -45,6 +45,10 @@ class SolveParams(ctypes.Structure):
                 ("m2", ctypes.c_double), ("shift", ctypes.c_double), ("precision", ctypes.c_int),
                 ("tol", ctypes.c_double), ("maxiter", ctypes.c_int), ("delta", ctypes.c_double),
                 ("use_x0", ctypes.c_int)]
+
+
+class Profile(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_longlong * 6), ("ms", ctypes.c_double * 6)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -93,6 +97,9 @@ def load_library(path: str = LIB_PATH):
         "eofa_link_update_dev": (I, [P, D, P, P, P]),
         "eofa_solve_batched": (I, [ctypes.POINTER(P), I, ctypes.POINTER(SolveParams), ctypes.POINTER(P),
                                    ctypes.POINTER(P), ctypes.POINTER(SolveInfo)]),
+        "eofa_kernel_launches": (LL, []),
+        "eofa_profile_start": (I, [P]),
+        "eofa_profile_stop": (I, [P, ctypes.POINTER(Profile)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -114,6 +121,11 @@ def _ptr(a) -> int:
 def _stream():
     import torch
     return torch.cuda.current_stream().cuda_stream
+
+
+def kernel_launches() -> int:
+    """Number of CUDA kernels libeofa has launched since it was loaded."""
+    return int(load_library().eofa_kernel_launches())
 
 
 def coefficients(Ls, alpha, m1, m2):
@@ -227,9 +239,10 @@ class Lattice:
         self._check(rc, "action")
         return S.value, info
 
-    def force(self, phi, alpha, M5, m1, m2, precision=PREC_F64, tol=1e-10):
+    def force(self, phi, alpha, M5, m1, m2, precision=PREC_F64, tol=1e-10, out=None):
         phi = np.ascontiguousarray(phi, dtype=np.complex128)
-        F = np.empty(self.shapeU, dtype=np.complex128)
+        F = np.empty(self.shapeU, dtype=np.complex128) if out is None else out
+        assert F.shape == self.shapeU and F.dtype == np.complex128 and F.flags["C_CONTIGUOUS"]
         S = ctypes.c_double()
         info = (SolveInfo * 2)()
         rc = self.lib.eofa_force(self.ctx, self.Ls, alpha, M5, m1, m2, precision, tol, _ptr(phi), _ptr(F),
@@ -287,6 +300,15 @@ class Lattice:
     def grad_from_chi_dev(self, k, chiL, chiR, G):
         self._check(self.lib.eofa_grad_from_chi_dev(self.ctx, k, _ptr(chiL), _ptr(chiR), _ptr(G), _stream()),
                     "grad_from_chi_dev")
+
+    def profile_start(self):
+        self._check(self.lib.eofa_profile_start(self.ctx), "profile_start")
+
+    def profile_stop(self):
+        """Per-kind (hop FP64/FP32/FP16, 5D-local FP64/FP32/FP16) launch counts and milliseconds."""
+        pr = Profile()
+        self._check(self.lib.eofa_profile_stop(self.ctx, ctypes.byref(pr)), "profile_stop")
+        return list(pr.launches), list(pr.ms)
 
     def link_update_dev(self, eps, P, U=None):
         self._check(self.lib.eofa_link_update_dev(self.ctx, eps, _ptr(P), _ptr(U) if U is not None else None,
