@@ -183,6 +183,30 @@ int eofa_link_update_dev(eofa_ctx* ctx, double eps, const double* P_dev, double*
 int eofa_solve_batched(eofa_ctx* const* ctxs, int n, const eofa_solve_params* params,
                        const double* const* b, double* const* x, eofa_solve_info* info);
 
+/* D_DWF in (dagger = 0) or D_DWF^+ in (dagger = 1) on device buffers, with
+ * the same arguments and result as eofa_dwf_apply_dev, but without
+ * allocating any device memory.  The paper has no counterpart: this is a
+ * service for callers that cannot call cudaMalloc when they apply the
+ * operator, such as applications that hand all GPU memory to their own pool
+ * allocator up front (a fresh cudaMalloc would fail or fragment the pool)
+ * and latency-critical loops that cannot afford cudaMalloc's implicit device
+ * synchronisation.
+ *   - Temporaries live in one 16 MiB static device array that every GPU
+ *     which loads libeofa keeps until the process exits.  Lattices needing
+ *     more (384 V Ls bytes > 16 MiB, e.g. anything above 8^4 x 8) are
+ *     rejected with EOFA_EINVAL and a message giving both sizes.
+ *   - The context must already exist with its gauge field loaded (those
+ *     calls allocate) and its device must be current (else EOFA_EINVAL).
+ *   - The first call on each device looks up the array's device address
+ *     with cudaGetSymbolAddress; make that first call before any stream
+ *     capture.
+ *   - Every call uses the same array: calls that overlap on the GPU (other
+ *     streams, threads or contexts at the same time) race and corrupt each
+ *     other's results.  Each call writes every temporary before reading it,
+ *     so nothing from an earlier call needs clearing. */
+int eofa_dwf_apply_noalloc(eofa_ctx* ctx, int Ls, double alpha, double M5, double mf, int dagger,
+                           const double* in_dev, double* out_dev, void* stream);
+
 /* Instrumentation.  eofa_kernel_launches: number of CUDA kernels this
  * library has launched since it was loaded (all contexts).
  * eofa_profile_start / _stop: while on, every even-odd hop and 5D-local

@@ -30,6 +30,7 @@ EXPORTS = [
     "eofa_solve", "eofa_solve_dev", "eofa_action", "eofa_action_dev", "eofa_force", "eofa_force_dev",
     "eofa_force_from_chi_dev", "eofa_grad_from_chi_dev", "eofa_coefficients", "eofa_link_update_dev",
     "eofa_solve_batched", "eofa_kernel_launches", "eofa_profile_start", "eofa_profile_stop",
+    "eofa_dwf_apply_noalloc",
 ]
 
 
@@ -98,6 +99,7 @@ def load_library(path: str = LIB_PATH):
         "eofa_solve_batched": (I, [ctypes.POINTER(P), I, ctypes.POINTER(SolveParams), ctypes.POINTER(P),
                                    ctypes.POINTER(P), ctypes.POINTER(SolveInfo)]),
         "eofa_kernel_launches": (LL, []),
+        "eofa_dwf_apply_noalloc": (I, [P, I, D, D, D, I, P, P, P]),
         "eofa_profile_start": (I, [P]),
         "eofa_profile_stop": (I, [P, ctypes.POINTER(Profile)]),
     }
@@ -269,6 +271,11 @@ class Lattice:
     def dwf_apply_dev(self, psi, out, alpha, M5, mf, dagger=False):
         self._check(self.lib.eofa_dwf_apply_dev(self.ctx, self.Ls, alpha, M5, mf, int(dagger), _ptr(psi), _ptr(out),
                                                 _stream()), "dwf_apply_dev")
+
+    def dwf_apply_noalloc_dev(self, psi, out, alpha, M5, mf, dagger=False):
+        """D_DWF (or D_DWF^+) without device allocation; see eofa_dwf_apply_noalloc in include/eofa.h."""
+        self._check(self.lib.eofa_dwf_apply_noalloc(self.ctx, self.Ls, alpha, M5, mf, int(dagger), _ptr(psi),
+                                                    _ptr(out), _stream()), "dwf_apply_noalloc")
 
     def solve_dev(self, b, x, use_x0=False, **kw):
         p = self.solve_params(use_x0=use_x0, **kw)
