@@ -164,7 +164,7 @@ def hop_only(args, wl):
     from paper_1611_00298_gb300 import build, eofa, inputs
     if not os.path.exists(eofa.LIB_PATH):
         build.build()
-    prec = {"f32": 1, "f16": 2}[args.precision]
+    prec = {"f64": 0, "f32": 1, "f16": 2}[args.hop_precision or args.precision]
     U = inputs.gauge_field(wl["dims"], wl["eps"], wl["seed"])
     lat = eofa.Lattice(wl["dims"], wl["Ls"], bc_t=wl["bc"])
     lat.gauge_load(U)
@@ -178,13 +178,17 @@ def hop_only(args, wl):
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record()
     for _ in range(args.hop_reps):
-        lat.hop_dev(prec, 0, 0, o, out)
+        if args.schur:
+            lat.schur_hop_dev(prec, 0, 0, o, out, wl["alpha"], wl["M5"], wl["m1"])
+        else:
+            lat.hop_dev(prec, 0, 0, o, out)
     ev1.record()
     torch.cuda.synchronize()
     ms = ev0.elapsed_time(ev1) / args.hop_reps
     n5h = lat.V // 2 * wl["Ls"]
     gbs = hop_bytes_per_site(prec, wl["Ls"]) * n5h / (ms / 1000) / 1e9
-    print(json.dumps({"hop_only": True, "dims": wl["dims"], "Ls": wl["Ls"], "precision": args.precision,
+    print(json.dumps({"hop_only": True, "schur": args.schur, "dims": wl["dims"], "Ls": wl["Ls"],
+                      "precision": args.hop_precision or args.precision,
                       "avg_ms": round(ms, 4), "GBs": round(gbs, 1), "kernel_version": kernel_version()}))
     lat.close()
     return 0
@@ -213,6 +217,8 @@ def main():
                     help="only launch the even-odd hop kernel (for ncu captures); see --dims, --hop-reps")
     ap.add_argument("--dims", default=None, help="X,Y,Z,T override for --hop-only")
     ap.add_argument("--hop-reps", type=int, default=4)
+    ap.add_argument("--schur", action="store_true", help="with --hop-only: the fused G^-1 D_hop kernel")
+    ap.add_argument("--hop-precision", default=None, choices=["f64", "f32", "f16"])
     args = ap.parse_args()
     wl = dict(SMALL if args.small else WORKLOAD)
     if args.dims:
@@ -378,7 +384,7 @@ def main():
 def kernel_version():
     """Hash of the hop kernel source, to invalidate stored ncu traffic when it changes."""
     import hashlib
-    src = open(os.path.join(ROOT, "paper_1611_00298_gb300", "csrc", "hop.cu"), "rb").read()
+    src = open(os.path.join(ROOT, "paper_1611_00298_gb300", "csrc", "dslash.cu"), "rb").read()
     return hashlib.sha256(src).hexdigest()[:16]
 
 

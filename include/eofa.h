@@ -118,6 +118,13 @@ int eofa_eofa_apply_dev(eofa_ctx* ctx, int Ls, double alpha, double M5, double m
 long long eofa_field_bytes(const eofa_ctx* ctx, int precision);
 int eofa_hop_dev(eofa_ctx* ctx, int precision, int out_parity, int dagger,
                  const void* in_dev, void* out_dev, void* stream);
+/* One half of the even-odd preconditioned operator of Eq. (3) in a single
+ * fused kernel: out = G^{-1} D_hop in (dagger = 0) or G^{-T} D_hop^+ in
+ * (dagger = 1), with D_hop the hop above and G = M D-tilde^{-1} the 5D-local
+ * block of D_EOFA = D_hop + G at mass mf (M = (4 - M5) D-tilde + 1 - L).
+ * Same buffers and layouts as eofa_hop_dev. */
+int eofa_schur_hop_dev(eofa_ctx* ctx, int precision, int out_parity, int dagger, int Ls, double alpha,
+                       double M5, double mf, const void* in_dev, void* out_dev, void* stream);
 /* Pack a canonical FP64 5D field (device) into the two half-checkerboard
  * device-layout fields of the given precision, and back. */
 int eofa_pack_dev(eofa_ctx* ctx, int precision, const double* canon_dev, void* even_dev,

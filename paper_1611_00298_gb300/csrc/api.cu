@@ -2,6 +2,7 @@
 // entry points.  Solves, action and force live in solver.cu and eofa.cu.
 #include "ops.h"
 #include "api_util.h"
+#include "fused.h"
 
 #include <cmath>
 #include <cstdio>
@@ -248,6 +249,23 @@ int eofa_hop_dev(eofa_ctx* ctx, int precision, int out_parity, int dagger, const
     try {
         require_gauge(ctx);
         launch_hop(ctx, precision, out_parity, dagger, in_dev, out_dev, (cudaStream_t)stream);
+    } catch (const eofa_error& e) {
+        return fail(ctx, e.code, e.msg);
+    }
+    return EOFA_OK;
+}
+
+int eofa_schur_hop_dev(eofa_ctx* ctx, int precision, int out_parity, int dagger, int Ls, double alpha, double M5,
+                       double mf, const void* in_dev, void* out_dev, void* stream) {
+    if (!ctx || !in_dev || !out_dev || precision < 0 || precision > 2 || (out_parity & ~1) || (dagger & ~1))
+        return fail(ctx, EOFA_EINVAL, "bad argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    try {
+        check_ls(ctx, Ls);
+        require_gauge(ctx);
+        System5 S = system_dwf(alpha, M5, mf);
+        Op5 op = dagger ? op_GinvT(ctx, S, 2, st) : op_Ginv(ctx, S, 0, st);
+        fused_dslash(ctx, precision, out_parity, dagger, in_dev, out_dev, op, nullptr, 1.0, 0.0, nullptr, 0, st);
     } catch (const eofa_error& e) {
         return fail(ctx, e.code, e.msg);
     }

@@ -7,13 +7,14 @@
 // are bitwise reproducible and need one launch.  Results land in
 // ctx->red[slot] (device) and are read back on demand.
 #include "field.cuh"
+#include "fused.h"
 
 #define RED_BLOCKS 608  // 4 x 152 SMs
 #define RED_THREADS 256
-// reduction scratch layout (doubles): [0, 64) results, [64, 64 + 2*RED_BLOCKS) partials,
-// then one unsigned ticket counter.
-#define RED_PART_OFF 64
-#define RED_TICKET_OFF (64 + 2 * RED_BLOCKS)
+// reduction scratch layout (doubles, see fused.h): [0, 64) results,
+// [128, 128 + 2*RED_BLOCKS) partials, then one unsigned ticket counter.
+#define RED_PART_OFF 128
+#define RED_TICKET_OFF (128 + 2 * RED_BLOCKS)
 
 namespace {
 
@@ -179,7 +180,8 @@ void red_fetch_many(const eofa_ctx* ctx, int first, int n, double* out, cudaStre
     for (int k = 0; k < n; k++) out[k] = ctx->red_host[k];
 }
 
-size_t red_scratch_bytes() { return (size_t)(RED_TICKET_OFF + 8) * sizeof(double); }
+size_t red_scratch_bytes() { return (size_t)RED_TOTAL_DOUBLES * sizeof(double); }
+static_assert(RED_TICKET_OFF + 8 <= RED_PART, "reduction scratch regions overlap");
 
 namespace {
 

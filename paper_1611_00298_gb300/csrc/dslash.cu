@@ -1,0 +1,45 @@
+// Precision dispatch of the fused solver kernels (dslash_impl.cuh).
+#include "dslash_impl.cuh"
+
+Op5 op_identity() {
+    Op5 op;
+    for (int h = 0; h < 2; h++) {
+        op.inv[h] = op.fwd[h] = 0;
+        op.p1[h] = op.q1[h] = op.p2[h] = op.q2[h] = 0.0;
+        op.dir1[h] = op.dir2[h] = 0;
+        op.sigma[h] = 0.0;
+        op.w[h] = op.v[h] = nullptr;
+    }
+    op.mass = 0.0;
+    op.a_out = 1.0;
+    op.b_in = 0.0;
+    return op;
+}
+
+void fused_dslash(const eofa_ctx* ctx, int prec, int out_parity, int dagger, const void* in, void* out, const Op5& op,
+                  const void* y, double a_out, double b_in, double* red, int slot, cudaStream_t st) {
+    const Op5 opf = op_finalize(op, ctx->Ls);
+    prof_begin(ctx, prec, st);
+    if (prec == P64) dslash_p64(ctx, out_parity, dagger, in, out, opf, y, a_out, b_in, red, slot, st);
+    else if (prec == P32) dslash_p32(ctx, out_parity, dagger, in, out, opf, y, a_out, b_in, red, slot, st);
+    else dslash_p16(ctx, out_parity, dagger, in, out, opf, y, a_out, b_in, red, slot, st);
+    prof_end(ctx, st);
+}
+
+void fused_local5(const eofa_ctx* ctx, int prec, const Op5& op, const void* x, const void* z, double c0,
+                  const double* sc, int it, int use_alpha, void* xw, void* out, double a_out, double* red, int slot,
+                  cudaStream_t st) {
+    const Op5 opf = op_finalize(op, ctx->Ls);
+    prof_begin(ctx, 3 + prec, st);
+    if (prec == P64) local5_p64(ctx, opf, x, z, c0, sc, it, use_alpha, xw, out, a_out, red, slot, st);
+    else if (prec == P32) local5_p32(ctx, opf, x, z, c0, sc, it, use_alpha, xw, out, a_out, red, slot, st);
+    else local5_p16(ctx, opf, x, z, c0, sc, it, use_alpha, xw, out, a_out, red, slot, st);
+    prof_end(ctx, st);
+}
+
+void fused_xp_update(const eofa_ctx* ctx, int prec, int precx, const double* sc, int it, void* x, void* p,
+                     const void* s, cudaStream_t st) {
+    if (prec == P64) xp_update_p64(ctx, sc, it, x, p, s, st);
+    else if (prec == P32) xp_update_p32(ctx, sc, it, x, p, s, st);
+    else xp_update_p16(ctx, sc, it, x, p, s, st);
+}

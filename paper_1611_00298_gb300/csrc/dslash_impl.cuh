@@ -1,0 +1,604 @@
+// Fused even-odd dslash kernels (templates; instantiated per storage
+// precision in dslash_p64.cu, dslash_p32.cu, dslash_p16.cu).
+//
+//   out = a (-1/2) B[ sum_mu hop terms ] + b y,    |out|^2 -> red[slot]
+//
+// The hop is the Wilson hopping term of Sec. 2 on every s-slice.  B is a
+// 5D-local block of Eq. (3) (Op5: per chirality an O(Ls) bidiagonal
+// inverse, a bidiagonal matrix and a rank-one term) or the identity.  A
+// block owns NS whole 4D sites x Ls slices:
+//   phase 1  one thread per (site, s) gathers the 8 neighbours (spin
+//            projection, one SU(3) link, reconstruction) into registers;
+//   phase 2  (B != 1) the 12 x Ls results go through shared memory and one
+//            thread per (site, component) runs the s-recurrences of B on
+//            its column held in registers (Ls is a template parameter for
+//            the common extents, so the recurrences unroll);
+//   phase 3  one thread per (site, s) applies the axpy, stores coalesced
+//            16-byte chunks and accumulates the norm.
+// The grid strides over tiles of NS sites; reductions have one partial per
+// block and a fixed-order final sum (bitwise reproducible).
+#pragma once
+#include "field.cuh"
+#include "fused.h"
+
+namespace dsl {
+namespace {
+
+// ---------------------------------------------------------------- hop pieces
+
+template <int MU, typename R>
+__device__ __forceinline__ void apply_A(const cpx<R>* l0, const cpx<R>* l1, cpx<R>* a0, cpx<R>* a1) {
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        if (MU == 0) { a0[c] = mitimes(l1[c]); a1[c] = mitimes(l0[c]); }
+        if (MU == 1) { a0[c] = mk(-l1[c].re, -l1[c].im); a1[c] = l0[c]; }
+        if (MU == 2) { a0[c] = mitimes(l0[c]); a1[c] = itimes(l1[c]); }
+        if (MU == 3) { a0[c] = l0[c]; a1[c] = l1[c]; }
+    }
+}
+
+// acc += (1 + SG gamma_mu) V psi (V = U or U^+), negated when neg.  The two
+// half-spinor rows are handled one after the other to keep few registers
+// live: row k contributes V h_k to acc[3k..3k+2] and SG (A^+ (V h))_k to the
+// lower spins.
+template <int MU, int SG, bool DAGLINK, typename R>
+__device__ __forceinline__ void hop_dir(const cpx<R>* psi, const Link<R>& U, bool neg, cpx<R>* acc) {
+    cpx<R> a0[3], a1[3];
+    apply_A<MU>(psi + 6, psi + 9, a0, a1);
+#pragma unroll
+    for (int row = 0; row < 2; row++) {
+        cpx<R> h[3], w[3];
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            cpx<R> a = row == 0 ? a0[c] : a1[c];
+            cpx<R> v = psi[3 * row + c];
+            h[c] = SG > 0 ? v + a : v - a;
+            if (neg) h[c] = mk(-h[c].re, -h[c].im);
+        }
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            if (DAGLINK) w[a] = cjmul(U.m[a], h[0]) + cjmul(U.m[3 + a], h[1]) + cjmul(U.m[6 + a], h[2]);
+            else w[a] = cmul(U.m[3 * a], h[0]) + cmul(U.m[3 * a + 1], h[1]) + cmul(U.m[3 * a + 2], h[2]);
+        }
+        // upper spin `row`
+#pragma unroll
+        for (int c = 0; c < 3; c++) acc[3 * row + c] = acc[3 * row + c] + w[c];
+        // lower spins: (A^+ W)_0 and (A^+ W)_1 in terms of W_row
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            cpx<R> t;
+            int dst;
+            if (MU == 0) { t = itimes(w[c]); dst = row == 0 ? 9 : 6; }               // (iW1, iW0)
+            else if (MU == 1) { t = row == 0 ? mk(-w[c].re, -w[c].im) : w[c]; dst = row == 0 ? 9 : 6; }  // (W1, -W0)
+            else if (MU == 2) { t = row == 0 ? itimes(w[c]) : mitimes(w[c]); dst = row == 0 ? 6 : 9; }   // (iW0, -iW1)
+            else { t = w[c]; dst = row == 0 ? 6 : 9; }                                  // (W0, W1)
+            acc[dst + c] = SG > 0 ? acc[dst + c] + t : acc[dst + c] - t;
+        }
+    }
+}
+
+template <int P, int DAG, int MU>
+__device__ __forceinline__ void hop_mu(const Geom& g, int par, int j, int s, int Ls, long long n5, const void* in,
+                                       const void* gauge, cpx<typename Field<P>::R>* acc) {
+    typedef typename Field<P>::R R;
+    cpx<R> psi[12];
+    Link<R> U;
+    const int* nb = par ? g.nbr[1] : g.nbr[0];
+    int e = __ldg(nb + (2 * MU) * g.Vh + j);
+    Field<P>::load(in, e & 0x7fffffff, s, Ls, n5, psi);
+    load_link<R>(gauge, (long long)((par * 4 + MU) * g.Vh + j), U);
+    hop_dir<MU, DAG ? 1 : -1, false>(psi, U, e < 0, acc);
+    e = __ldg(nb + (2 * MU + 1) * g.Vh + j);
+    const int jn = e & 0x7fffffff;
+    Field<P>::load(in, jn, s, Ls, n5, psi);
+    load_link<R>(gauge, (long long)(((1 - par) * 4 + MU) * g.Vh + jn), U);
+    hop_dir<MU, DAG ? -1 : 1, true>(psi, U, e < 0, acc);
+}
+
+// ---------------------------------------------------------------- 5D-local column ops
+//
+// Column x[0..Ls) of one (site, component); B = p + q L_dir with L_dir the
+// down-shift (dir 0) or up-shift (dir 1), corner -mass.  The inverse uses
+// L^Ls = -mass: u_0 = [x_0 - mass sum_{j>=1} (-r)^(Ls-j) x_j] / (p (1 + mass (-r)^Ls)),
+// u_s = (x_s - q u_{s-1}) / p (mirrored for dir 1).
+
+// runtime-Ls versions working in shared memory (fallback for uncommon Ls)
+template <typename R>
+__device__ void sm_inv(cpx<R>* x, int Ls, R p, R q, int dir, R mass) {
+    const R mr = -q / p;
+    R pw = 1;
+    for (int k = 0; k < Ls; k++) pw *= mr;
+    const R invN = R(1) / (p * (R(1) + mass * pw));
+    const R invp = R(1) / p;
+    cpx<R> acc = mk(R(0), R(0));
+    if (dir == 0) {
+        for (int s = 1; s < Ls; s++) acc = mr * acc + x[s];
+        acc = mr * acc;
+        x[0] = invN * (x[0] - mass * acc);
+        for (int s = 1; s < Ls; s++) x[s] = invp * (x[s] - q * x[s - 1]);
+    } else {
+        for (int s = Ls - 2; s >= 0; s--) acc = mr * acc + x[s];
+        acc = mr * acc;
+        x[Ls - 1] = invN * (x[Ls - 1] - mass * acc);
+        for (int s = Ls - 2; s >= 0; s--) x[s] = invp * (x[s] - q * x[s + 1]);
+    }
+}
+
+template <typename R>
+__device__ void sm_fwd(cpx<R>* x, int Ls, R p, R q, int dir, R mass) {
+    if (dir == 0) {
+        const cpx<R> last = x[Ls - 1];
+        for (int s = Ls - 1; s >= 1; s--) x[s] = p * x[s] + q * x[s - 1];
+        x[0] = p * x[0] - (q * mass) * last;
+    } else {
+        const cpx<R> first = x[0];
+        for (int s = 0; s < Ls - 1; s++) x[s] = p * x[s] + q * x[s + 1];
+        x[Ls - 1] = p * x[Ls - 1] - (q * mass) * first;
+    }
+}
+
+// per-chirality parameters of an Op5 without dynamic indexing of the struct
+template <typename R>
+struct Half {
+    int inv, fwd, dir1, dir2;
+    R p1, q1, p2, q2, sigma, mass, mr, invp, invN;
+    const double *w, *v;
+};
+
+template <typename R>
+__device__ __forceinline__ Half<R> half_of(const Op5& op, int h) {
+    Half<R> H;
+    H.inv = h ? op.inv[1] : op.inv[0];
+    H.fwd = h ? op.fwd[1] : op.fwd[0];
+    H.dir1 = h ? op.dir1[1] : op.dir1[0];
+    H.dir2 = h ? op.dir2[1] : op.dir2[0];
+    H.p1 = (R)(h ? op.p1[1] : op.p1[0]);
+    H.q1 = (R)(h ? op.q1[1] : op.q1[0]);
+    H.p2 = (R)(h ? op.p2[1] : op.p2[0]);
+    H.q2 = (R)(h ? op.q2[1] : op.q2[0]);
+    H.sigma = (R)(h ? op.sigma[1] : op.sigma[0]);
+    H.mass = (R)op.mass;
+    H.mr = (R)(h ? op.mr[1] : op.mr[0]);
+    H.invp = (R)(h ? op.invp[1] : op.invp[0]);
+    H.invN = (R)(h ? op.invN[1] : op.invN[0]);
+    H.w = h ? op.w[1] : op.w[0];
+    H.v = h ? op.v[1] : op.v[0];
+    return H;
+}
+
+// Streaming form of B for a compile-time Ls when the inverse and the matrix
+// use the same shift direction (every block built in ops.cu): one pass for
+// the Horner sum of the corner term, one pass that runs the inverse
+// recurrence u_s and emits (p2 + q2 L) u on the fly; two live values per
+// step instead of the whole column.
+template <typename R>
+struct Vec2;
+template <>
+struct Vec2<float> {
+    typedef float2 T;
+};
+template <>
+struct Vec2<double> {
+    typedef double2 T;
+};
+
+template <typename R>
+__device__ __forceinline__ cpx<R> lds(const cpx<R>* p) {
+    typename Vec2<R>::T v = *reinterpret_cast<const typename Vec2<R>::T*>(p);
+    return mk(v.x, v.y);
+}
+
+template <typename R>
+__device__ __forceinline__ void sts(cpx<R>* p, cpx<R> a) {
+    typename Vec2<R>::T v;
+    v.x = a.re;
+    v.y = a.im;
+    *reinterpret_cast<typename Vec2<R>::T*>(p) = v;
+}
+
+template <typename R, int LS, bool R1>
+__device__ __forceinline__ void col_stream(const Half<R>& H, cpx<R>* col) {
+    const R q = H.q1, mass = H.mass, mr = H.mr, invp = H.invp, invN = H.invN;
+    const R p2 = H.fwd ? H.p2 : R(1), q2 = H.fwd ? H.q2 : R(0);
+    cpx<R> acc = mk(R(0), R(0)), d = mk(R(0), R(0));
+    if (H.dir1 == 0) {
+#pragma unroll
+        for (int s = 1; s < LS; s++) acc = mr * acc + lds(col + s);
+        acc = mr * acc;
+        const cpx<R> u0 = invN * (lds(col) - mass * acc);
+        cpx<R> u = u0;
+        if (R1) d = (R)__ldg(H.v) * u0;
+#pragma unroll
+        for (int s = 1; s < LS; s++) {
+            const cpx<R> un = invp * (lds(col + s) - q * u);
+            if (R1) d = d + (R)__ldg(H.v + s) * un;
+            sts(col + s, p2 * un + q2 * u);
+            u = un;
+        }
+        sts(col, p2 * u0 - (q2 * mass) * u);
+    } else {
+#pragma unroll
+        for (int s = LS - 2; s >= 0; s--) acc = mr * acc + lds(col + s);
+        acc = mr * acc;
+        const cpx<R> uL = invN * (lds(col + LS - 1) - mass * acc);
+        cpx<R> u = uL;
+        if (R1) d = (R)__ldg(H.v + LS - 1) * uL;
+#pragma unroll
+        for (int s = LS - 2; s >= 0; s--) {
+            const cpx<R> un = invp * (lds(col + s) - q * u);
+            if (R1) d = d + (R)__ldg(H.v + s) * un;
+            sts(col + s, p2 * un + q2 * u);
+            u = un;
+        }
+        sts(col + LS - 1, p2 * uL - (q2 * mass) * u);
+    }
+    if (R1) {
+        // rank-one term: out += sigma w (v . u), u the inverse's result
+        const cpx<R> sd = H.sigma * d;
+#pragma unroll
+        for (int s = 0; s < LS; s++) sts(col + s, lds(col + s) + (R)__ldg(H.w + s) * sd);
+    }
+}
+
+// apply B to the column at col (shared memory, stride 1, length Ls)
+template <typename R, int LS>
+__device__ __forceinline__ void column_op(const Op5& op, int c, cpx<R>* col, int Ls) {
+    const Half<R> H = half_of<R>(op, c < 6 ? 0 : 1);
+    if (LS > 0 && H.inv && (!H.fwd || H.dir2 == H.dir1)) {
+        if (H.sigma == R(0)) col_stream<R, (LS > 0 ? LS : 1), false>(H, col);
+        else col_stream<R, (LS > 0 ? LS : 1), true>(H, col);
+        return;
+    }
+    if (H.inv) sm_inv<R>(col, Ls, H.p1, H.q1, H.dir1, H.mass);
+    cpx<R> d = mk(R(0), R(0));
+    if (H.sigma != R(0))
+        for (int s = 0; s < Ls; s++) d = d + (R)__ldg(H.v + s) * col[s];
+    if (H.fwd) sm_fwd<R>(col, Ls, H.p2, H.q2, H.dir2, H.mass);
+    if (H.sigma != R(0)) {
+        const cpx<R> sd = H.sigma * d;
+        for (int s = 0; s < Ls; s++) col[s] = col[s] + (R)__ldg(H.w + s) * sd;
+    }
+}
+
+__device__ __forceinline__ bool op_is_identity(const Op5& op) {
+    return !op.inv[0] && !op.inv[1] && !op.fwd[0] && !op.fwd[1] && op.sigma[0] == 0.0 && op.sigma[1] == 0.0;
+}
+
+// ---------------------------------------------------------------- reductions
+
+__device__ __forceinline__ double warp_sum(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Sum v over the block, then over the grid (last block, fixed order) into red[slot].
+__device__ __noinline__ void grid_sum(double v, double* red, int slot) {
+    __shared__ double ws[32];
+    __shared__ bool last;
+    v = warp_sum(v);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = (blockDim.x + 31) >> 5;
+    if (l == 0) ws[w] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0;
+        for (int k = 0; k < nw; k++) t += ws[k];
+        red[RED_PART + blockIdx.x] = t;
+        __threadfence();
+        unsigned prev = atomicAdd((unsigned*)(red + RED_TICKET), 1u);
+        last = prev == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (last) {
+        __threadfence();
+        double t = 0;
+        for (int k = threadIdx.x; k < (int)gridDim.x; k += blockDim.x) t += ((volatile double*)red)[RED_PART + k];
+        t = warp_sum(t);
+        __syncthreads();
+        if (l == 0) ws[w] = t;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double f = 0;
+            for (int k = 0; k < nw; k++) f += ws[k];
+            red[slot] = f;
+            *(unsigned*)(red + RED_TICKET) = 0u;
+        }
+    }
+}
+
+template <typename R>
+__device__ __forceinline__ double site_norm2(const cpx<R>* v) {
+    R a = 0;
+#pragma unroll
+    for (int c = 0; c < 12; c++) a += v[c].re * v[c].re + v[c].im * v[c].im;
+    return (double)a;
+}
+
+__device__ __forceinline__ double cg_alpha(const double* sc, int it) {
+    const double gam = sc[SC_GAMMA + (it & 1)], del = sc[SC_DELTA];
+    return (del > 0.0 && gam > 0.0) ? gam / del : 0.0;
+}
+
+__device__ __forceinline__ double cg_beta(const double* sc, int it) {
+    const double gold = sc[SC_GAMMA + (it & 1)], gnew = sc[SC_GAMMA + ((it + 1) & 1)];
+    return gold > 0.0 ? gnew / gold : 0.0;
+}
+
+// ---------------------------------------------------------------- fused dslash
+
+template <int P, int DAG, int LS>
+__global__ void __launch_bounds__(256, 3) dslash_kernel(Geom g, int par, const void* __restrict__ in, void* out,
+                                                     const void* __restrict__ gauge, Op5 op, const void* y,
+                                                     double a_out, double b_in, double* red, int slot, int NS) {
+    typedef typename Field<P>::R R;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    cpx<R>* sm = reinterpret_cast<cpx<R>*>(smraw);
+    const int Ls = LS > 0 ? LS : g.Ls;
+    const int LsP = Ls + 1;
+    const long long n5 = (long long)g.Vh * Ls;
+    const int ls = threadIdx.x / Ls, s = threadIdx.x - ls * Ls;
+    const bool active_thread = ls < NS;
+    const bool ident = op_is_identity(op);
+    const int ntiles = (g.Vh + NS - 1) / NS;
+    const R scale = (R)(-0.5 * a_out);
+    double nacc = 0.0;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int j = tile * NS + ls;
+        const bool site_ok = active_thread && j < g.Vh;
+        cpx<R> acc[12];
+#pragma unroll
+        for (int c = 0; c < 12; c++) acc[c] = mk(R(0), R(0));
+        if (site_ok) {
+            hop_mu<P, DAG, 0>(g, par, j, s, Ls, n5, in, gauge, acc);
+            hop_mu<P, DAG, 1>(g, par, j, s, Ls, n5, in, gauge, acc);
+            hop_mu<P, DAG, 2>(g, par, j, s, Ls, n5, in, gauge, acc);
+            hop_mu<P, DAG, 3>(g, par, j, s, Ls, n5, in, gauge, acc);
+        }
+        if (!ident) {
+            if (site_ok) {
+#pragma unroll
+                for (int c = 0; c < 12; c++) sts(sm + (ls * 12 + c) * LsP + s, acc[c]);
+            }
+            __syncthreads();
+            const int nsites = min(NS, g.Vh - tile * NS);
+            for (int idx = threadIdx.x; idx < nsites * 12; idx += blockDim.x)
+                column_op<R, LS>(op, idx % 12, sm + idx * LsP, Ls);
+            __syncthreads();
+            if (site_ok) {
+#pragma unroll
+                for (int c = 0; c < 12; c++) acc[c] = lds(sm + (ls * 12 + c) * LsP + s);
+            }
+        }
+        if (site_ok) {
+#pragma unroll
+            for (int c = 0; c < 12; c++) acc[c] = scale * acc[c];
+            if (y != nullptr) {
+                cpx<R> yv[12];
+                Field<P>::load(y, j, s, Ls, n5, yv);
+                const R bb = (R)b_in;
+#pragma unroll
+                for (int c = 0; c < 12; c++) acc[c] = acc[c] + bb * yv[c];
+            }
+            Field<P>::store(out, j, s, Ls, n5, acc);
+            if (red) nacc += site_norm2<R>(acc);
+        }
+        if (!ident) __syncthreads();
+    }
+    if (red) grid_sum(nacc, red, slot);
+}
+
+// x' = x + c z (c = -alpha from the device scalars when use_alpha, else c0);
+// xw <- x' (if xw), |x'|^2 -> red[slot] (if red), out = a B x' (if out).
+template <int P, int LS>
+__global__ void __launch_bounds__(256, 3) local5_kernel(Geom g, Op5 op, const void* x, const void* z, double c0,
+                                                     const double* sc, int it, int use_alpha, void* xw, void* out,
+                                                     double a_out, double* red, int slot, int NS) {
+    typedef typename Field<P>::R R;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    cpx<R>* sm = reinterpret_cast<cpx<R>*>(smraw);
+    const int Ls = LS > 0 ? LS : g.Ls;
+    const int LsP = Ls + 1;
+    const long long n5 = (long long)g.Vh * Ls;
+    const int ls = threadIdx.x / Ls, s = threadIdx.x - ls * Ls;
+    const bool active_thread = ls < NS;
+    const bool ident = op_is_identity(op);
+    const int ntiles = (g.Vh + NS - 1) / NS;
+    const R c = (R)(use_alpha ? -cg_alpha(sc, it) : c0);
+    double nacc = 0.0;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int j = tile * NS + ls;
+        const bool site_ok = active_thread && j < g.Vh;
+        cpx<R> v[12];
+        if (site_ok) {
+            Field<P>::load(x, j, s, Ls, n5, v);
+            if (z != nullptr) {
+                cpx<R> zv[12];
+                Field<P>::load(z, j, s, Ls, n5, zv);
+#pragma unroll
+                for (int k = 0; k < 12; k++) v[k] = v[k] + c * zv[k];
+            }
+            if (xw) Field<P>::store(xw, j, s, Ls, n5, v);
+            if (red) nacc += site_norm2<R>(v);
+        }
+        if (out) {
+            if (!ident) {
+                if (site_ok) {
+#pragma unroll
+                    for (int k = 0; k < 12; k++) sts(sm + (ls * 12 + k) * LsP + s, v[k]);
+                }
+                __syncthreads();
+                const int nsites = min(NS, g.Vh - tile * NS);
+                for (int idx = threadIdx.x; idx < nsites * 12; idx += blockDim.x)
+                    column_op<R, LS>(op, idx % 12, sm + idx * LsP, Ls);
+                __syncthreads();
+                if (site_ok) {
+#pragma unroll
+                    for (int k = 0; k < 12; k++) v[k] = lds(sm + (ls * 12 + k) * LsP + s);
+                }
+            }
+            if (site_ok) {
+#pragma unroll
+                for (int k = 0; k < 12; k++) v[k] = (R)a_out * v[k];
+                Field<P>::store(out, j, s, Ls, n5, v);
+            }
+            if (!ident) __syncthreads();
+        }
+    }
+    if (red) grid_sum(nacc, red, slot);
+}
+
+// x += alpha p (x in PX), p = s + beta p
+template <int P, int PX>
+__global__ void __launch_bounds__(256) xp_update_kernel(Geom g, const double* sc, int it, void* x, void* p,
+                                                        const void* s) {
+    typedef typename Field<P>::R R;
+    typedef typename Field<PX>::R RX;
+    const long long n5 = (long long)g.Vh * g.Ls;
+    const R alpha = (R)cg_alpha(sc, it), beta = (R)cg_beta(sc, it);
+    const unsigned n5u = (unsigned)n5, Lsu = (unsigned)g.Ls;
+    for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < n5u; t += gridDim.x * blockDim.x) {
+        const int j = (int)(t / Lsu);
+        const int ss = (int)(t - (unsigned)j * Lsu);
+        cpx<R> pv[12], sv[12];
+        cpx<RX> xv[12];
+        Field<P>::load(p, j, ss, g.Ls, n5, pv);
+        Field<P>::load(s, j, ss, g.Ls, n5, sv);
+        Field<PX>::load(x, j, ss, g.Ls, n5, xv);
+#pragma unroll
+        for (int k = 0; k < 12; k++) {
+            xv[k] = mk((RX)(xv[k].re + (RX)alpha * (RX)pv[k].re), (RX)(xv[k].im + (RX)alpha * (RX)pv[k].im));
+            pv[k] = sv[k] + beta * pv[k];
+        }
+        Field<PX>::store(x, j, ss, g.Ls, n5, xv);
+        Field<P>::store(p, j, ss, g.Ls, n5, pv);
+    }
+}
+
+// ---------------------------------------------------------------- launch helpers
+
+// sites per tile: NS * Ls a multiple of 32 where possible, 96..256 threads,
+// at most 32 KB of shared memory
+inline int pick_ns(int Ls, size_t elem) {
+    int gg = 1;
+    for (int k = 32; k >= 1; k >>= 1)
+        if (Ls % k == 0) { gg = k; break; }
+    int ns = 32 / gg;
+    while (ns * Ls < 96) ns *= 2;
+    while (ns * Ls > 256 && ns > 1) ns /= 2;
+    while ((size_t)ns * 12 * (Ls + 1) * elem > 32768 && ns > 1) ns /= 2;
+    if (ns < 1) ns = 1;
+    return ns;
+}
+
+template <typename K>
+unsigned grid_size(K kernel, int threads, size_t smem, int ntiles, int sms) {
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem);
+    if (per_sm < 1) per_sm = 1;
+    long long cap = (long long)per_sm * sms;
+    if (cap > RED_MAX_BLOCKS) cap = RED_MAX_BLOCKS;
+    return (unsigned)(ntiles < cap ? (ntiles > 0 ? ntiles : 1) : cap);
+}
+
+template <int P, int DAG, int LS>
+void launch_dslash_t(const eofa_ctx* ctx, int par, const void* in, void* out, const Op5& op, const void* y,
+                     double a_out, double b_in, double* red, int slot, cudaStream_t st) {
+    typedef typename Field<P>::R R;
+    Geom g = ctx_geom(ctx);
+    const int NS = pick_ns(g.Ls, sizeof(cpx<R>));
+    const int threads = (NS * g.Ls + 31) / 32 * 32;
+    const size_t smem = (size_t)NS * 12 * (g.Ls + 1) * sizeof(cpx<R>);
+    const int ntiles = (g.Vh + NS - 1) / NS;
+    const void* gauge = ctx->gauge[P == P64 ? P64 : P32];
+    auto k = dslash_kernel<P, DAG, LS>;
+    if (smem > 40 * 1024) EOFA_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    unsigned grid = grid_size(k, threads, smem, ntiles, ctx->sms);
+    k<<<grid, threads, smem, st>>>(g, par, in, out, gauge, op, y, a_out, b_in, red, slot, NS);
+    EOFA_LAUNCHED();
+}
+
+template <int P, int LS>
+void launch_local5_t(const eofa_ctx* ctx, const Op5& op, const void* x, const void* z, double c0, const double* sc,
+                     int it, int use_alpha, void* xw, void* out, double a_out, double* red, int slot, cudaStream_t st) {
+    typedef typename Field<P>::R R;
+    Geom g = ctx_geom(ctx);
+    const int NS = pick_ns(g.Ls, sizeof(cpx<R>));
+    const int threads = (NS * g.Ls + 31) / 32 * 32;
+    const size_t smem = (size_t)NS * 12 * (g.Ls + 1) * sizeof(cpx<R>);
+    const int ntiles = (g.Vh + NS - 1) / NS;
+    auto k = local5_kernel<P, LS>;
+    if (smem > 40 * 1024) EOFA_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    unsigned grid = grid_size(k, threads, smem, ntiles, ctx->sms);
+    k<<<grid, threads, smem, st>>>(g, op, x, z, c0, sc, it, use_alpha, xw, out, a_out, red, slot, NS);
+    EOFA_LAUNCHED();
+}
+
+// dispatch on Ls: unrolled columns for the common extents, shared-memory loops otherwise
+template <int P>
+void dslash_prec(const eofa_ctx* ctx, int par, int dag, const void* in, void* out, const Op5& op, const void* y,
+                 double a_out, double b_in, double* red, int slot, cudaStream_t st) {
+#define DSL_CASE(L)                                                                             \
+    if (dag) launch_dslash_t<P, 1, L>(ctx, par, in, out, op, y, a_out, b_in, red, slot, st);   \
+    else launch_dslash_t<P, 0, L>(ctx, par, in, out, op, y, a_out, b_in, red, slot, st);
+    switch (ctx->Ls) {
+        case 8: DSL_CASE(8) break;
+        case 12: DSL_CASE(12) break;
+        case 16: DSL_CASE(16) break;
+        case 24: DSL_CASE(24) break;
+        default: DSL_CASE(0) break;
+    }
+#undef DSL_CASE
+}
+
+template <int P>
+void local5_prec(const eofa_ctx* ctx, const Op5& op, const void* x, const void* z, double c0, const double* sc,
+                 int it, int use_alpha, void* xw, void* out, double a_out, double* red, int slot, cudaStream_t st) {
+    switch (ctx->Ls) {
+        case 8: launch_local5_t<P, 8>(ctx, op, x, z, c0, sc, it, use_alpha, xw, out, a_out, red, slot, st); break;
+        case 12: launch_local5_t<P, 12>(ctx, op, x, z, c0, sc, it, use_alpha, xw, out, a_out, red, slot, st); break;
+        case 16: launch_local5_t<P, 16>(ctx, op, x, z, c0, sc, it, use_alpha, xw, out, a_out, red, slot, st); break;
+        case 24: launch_local5_t<P, 24>(ctx, op, x, z, c0, sc, it, use_alpha, xw, out, a_out, red, slot, st); break;
+        default: launch_local5_t<P, 0>(ctx, op, x, z, c0, sc, it, use_alpha, xw, out, a_out, red, slot, st); break;
+    }
+}
+
+template <int P, int PX>
+void xp_update_prec(const eofa_ctx* ctx, const double* sc, int it, void* x, void* p, const void* s, cudaStream_t st) {
+    Geom g = ctx_geom(ctx);
+    long long n5 = (long long)g.Vh * g.Ls;
+    long long nb = (n5 + 255) / 256;
+    long long cap = (long long)ctx->sms * 8;
+    unsigned grid = (unsigned)(nb < cap ? nb : cap);
+    xp_update_kernel<P, PX><<<grid, 256, 0, st>>>(g, sc, it, x, p, s);
+    EOFA_LAUNCHED();
+}
+
+}  // namespace
+}  // namespace dsl
+
+// per-precision entry points (dslash_p64.cu, dslash_p32.cu, dslash_p16.cu)
+#define DSL_DECLARE(NAME)                                                                                        \
+    void dslash_##NAME(const eofa_ctx* ctx, int par, int dag, const void* in, void* out, const Op5& op,         \
+                       const void* y, double a_out, double b_in, double* red, int slot, cudaStream_t st);       \
+    void local5_##NAME(const eofa_ctx* ctx, const Op5& op, const void* x, const void* z, double c0,            \
+                       const double* sc, int it, int use_alpha, void* xw, void* out, double a_out, double* red, \
+                       int slot, cudaStream_t st);                                                              \
+    void xp_update_##NAME(const eofa_ctx* ctx, const double* sc, int it, void* x, void* p, const void* s,      \
+                          cudaStream_t st);
+DSL_DECLARE(p64)
+DSL_DECLARE(p32)
+DSL_DECLARE(p16)
+
+#define DSL_DEFINE(NAME, P, PX)                                                                                  \
+    void dslash_##NAME(const eofa_ctx* ctx, int par, int dag, const void* in, void* out, const Op5& op,         \
+                       const void* y, double a_out, double b_in, double* red, int slot, cudaStream_t st) {      \
+        dsl::dslash_prec<P>(ctx, par, dag, in, out, op, y, a_out, b_in, red, slot, st);                        \
+    }                                                                                                           \
+    void local5_##NAME(const eofa_ctx* ctx, const Op5& op, const void* x, const void* z, double c0,            \
+                       const double* sc, int it, int use_alpha, void* xw, void* out, double a_out, double* red, \
+                       int slot, cudaStream_t st) {                                                             \
+        dsl::local5_prec<P>(ctx, op, x, z, c0, sc, it, use_alpha, xw, out, a_out, red, slot, st);               \
+    }                                                                                                           \
+    void xp_update_##NAME(const eofa_ctx* ctx, const double* sc, int it, void* x, void* p, const void* s,      \
+                          cudaStream_t st) {                                                                    \
+        dsl::xp_update_prec<P, PX>(ctx, sc, it, x, p, s, st);                                                   \
+    }

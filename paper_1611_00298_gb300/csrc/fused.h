@@ -1,0 +1,30 @@
+// Fused kernels of the solver hot loop (dslash.cu) and the device-scalar layout.
+#pragma once
+#include "internal.h"
+
+// Layout of ctx->red (doubles):
+//   [0, 64)              results of the generic reductions (blas.cu)
+//   [SC_RRH, +32)        |r|^2 history ring of the CG (index it % 32)
+//   SC_GAMMA, +1         gamma = |A^+ r|^2, double-buffered by iteration parity
+//   SC_DELTA             delta = |A p|^2
+//   [128, 1344), 1344    partials and ticket of the generic reductions
+//   [RED_PART, +RED_MAX_BLOCKS), RED_TICKET   partials and ticket of the fused kernels
+#define SC_RRH 64
+#define SC_GAMMA 96
+#define SC_DELTA 98
+#define RED_PART 2048
+#define RED_MAX_BLOCKS 4096
+#define RED_TICKET (RED_PART + RED_MAX_BLOCKS)
+#define RED_TOTAL_DOUBLES (RED_TICKET + 8)
+
+// out = a_out * (-1/2) B[hop(in)] + b_in * y ; |out|^2 -> red[slot] if red
+void fused_dslash(const eofa_ctx* ctx, int prec, int out_parity, int dagger, const void* in, void* out, const Op5& op,
+                  const void* y, double a_out, double b_in, double* red, int slot, cudaStream_t st);
+// x' = x + c z (c = -alpha(sc, it) if use_alpha else c0); xw <- x'; |x'|^2 -> red[slot]; out = a_out B x'
+void fused_local5(const eofa_ctx* ctx, int prec, const Op5& op, const void* x, const void* z, double c0,
+                  const double* sc, int it, int use_alpha, void* xw, void* out, double a_out, double* red, int slot,
+                  cudaStream_t st);
+// x += alpha p ; p = s + beta p   (alpha, beta from sc at iteration it)
+void fused_xp_update(const eofa_ctx* ctx, int prec, int precx, const double* sc, int it, void* x, void* p,
+                     const void* s, cudaStream_t st);
+Op5 op_identity();

@@ -85,7 +85,11 @@ struct Op5 {
     const double* w[2];  // device, Ls each
     const double* v[2];
     double a_out, b_in;  // out = a_out * op(x) + b_in * y
+    // derived constants of the inverse (filled by op_finalize on the host):
+    // mr = -q1/p1, invp = 1/p1, invN = 1/(p1 (1 + mass mr^Ls))
+    double mr[2], invp[2], invN[2];
 };
+Op5 op_finalize(Op5 op, int Ls);
 
 // Kernel launch accounting and optional per-kernel CUDA-event timing.
 struct Prof {

@@ -118,7 +118,7 @@ void run_op5(const eofa_ctx* ctx, const Op5& op, const void* x, const void* y, v
     if (NS > 32) NS = 32;
     size_t smem = per_site * NS;
     unsigned nb = (unsigned)((g.Vh + NS - 1) / NS);
-    if (smem > 48 * 1024) EOFA_CUDA(cudaFuncSetAttribute(op5_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    if (smem > 40 * 1024) EOFA_CUDA(cudaFuncSetAttribute(op5_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     prof_begin(ctx, 3 + P, st);
     op5_kernel<P><<<nb, 128, smem, st>>>(g, op, NS, x, y, out);
     EOFA_LAUNCHED();

@@ -107,6 +107,19 @@ Op5 op_base() {
 
 }  // namespace
 
+Op5 op_finalize(Op5 op, int Ls) {
+    for (int h = 0; h < 2; h++) {
+        if (op.inv[h]) {
+            op.mr[h] = -op.q1[h] / op.p1[h];
+            op.invp[h] = 1.0 / op.p1[h];
+            op.invN[h] = 1.0 / (op.p1[h] * (1.0 + op.mass * std::pow(op.mr[h], Ls)));
+        } else {
+            op.mr[h] = op.invp[h] = op.invN[h] = 0.0;
+        }
+    }
+    return op;
+}
+
 Coeffs make_coeffs(double alpha, double M5, double m) {
     Coeffs k;
     double c = 0.5 * alpha, d = 0.5;

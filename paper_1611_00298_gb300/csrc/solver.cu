@@ -15,6 +15,9 @@
 // updates), and the solution accumulates in FP64.  The stopping test is the
 // FP64 true residual of the full, unpreconditioned system.
 #include "api_util.h"
+#include "fused.h"
+
+#include <algorithm>
 
 #include <chrono>
 #include <cmath>
@@ -25,31 +28,21 @@ struct SchurOps {
     Op5 Gi, GiT;
 };
 
-struct Work {
-    int prec;   // inner storage precision
-    int precx;  // inner solution accumulator precision
-    void *p, *q, *r, *s, *x, *te, *te2, *to;
-};
-
-// out = A in (odd -> odd), precision w.prec
-void apply_A(eofa_ctx* ctx, const SchurOps& o, int prec, const void* in, void* out, void* te, void* te2, cudaStream_t st) {
-    launch_hop(ctx, prec, 0, 0, in, te, st);
-    launch_op5(ctx, prec, o.Gi, te, nullptr, te2, st);
-    launch_hop(ctx, prec, 1, 0, te2, out, st);
-    Op5 g = o.Gi;
-    g.a_out = -1.0;
-    g.b_in = 1.0;
-    launch_op5(ctx, prec, g, out, in, out, st);
+// out = A in (odd -> odd) with the fused kernels; |out|^2 -> red[slot] if red
+void apply_A(eofa_ctx* ctx, const SchurOps& o, int prec, const void* in, void* out, void* te, double* red, int slot,
+             cudaStream_t st) {
+    fused_dslash(ctx, prec, 0, 0, in, te, o.Gi, nullptr, 1.0, 0.0, nullptr, 0, st);
+    fused_dslash(ctx, prec, 1, 0, te, out, o.Gi, in, -1.0, 1.0, red, slot, st);
 }
 
-// out = A^+ in; to is an odd temporary
-void apply_Adag(eofa_ctx* ctx, const SchurOps& o, int prec, const void* in, void* out, void* te, void* te2, void* to,
-                cudaStream_t st) {
-    launch_op5(ctx, prec, o.GiT, in, nullptr, to, st);
-    launch_hop(ctx, prec, 0, 1, to, te, st);
-    launch_op5(ctx, prec, o.GiT, te, nullptr, te2, st);
-    launch_hop(ctx, prec, 1, 1, te2, out, st);
-    blas_axpby(ctx, prec, 1.0, in, -1.0, out, st);
+// s = A^+ r' where r' = r - alpha q (when q; written back to r) and |r'|^2 -> red[rslot];
+// |s|^2 -> red[gslot]
+void apply_Adag_cg(eofa_ctx* ctx, const SchurOps& o, int prec, void* r, const void* q, int it, void* s, void* te,
+                   void* to, int rslot, int gslot, cudaStream_t st) {
+    fused_local5(ctx, prec, o.GiT, r, q, 0.0, ctx->red, it, q != nullptr, q != nullptr ? r : nullptr, to, 1.0,
+                 ctx->red, rslot, st);
+    fused_dslash(ctx, prec, 0, 1, to, te, o.GiT, nullptr, 1.0, 0.0, nullptr, 0, st);
+    fused_dslash(ctx, prec, 1, 1, te, s, op_identity(), r, -1.0, 1.0, ctx->red, gslot, st);
 }
 
 double norm2_now(eofa_ctx* ctx, int prec, const void* x, cudaStream_t st) {
@@ -98,7 +91,6 @@ int solve_dev_impl(eofa_ctx* ctx, const eofa_solve_params* prm, const double* b_
     void* x_o = ctx_buffer(ctx, "sv_xo", f64);
     void* r64 = ctx_buffer(ctx, "sv_r64", f64);
     void* a_e = ctx_buffer(ctx, "sv_ae", f64);
-    void* a_e2 = ctx_buffer(ctx, "sv_ae2", f64);
     void* a_o = ctx_buffer(ctx, "sv_ao", f64);
 
     // right-hand side of (D_hop + G') psi = f
@@ -117,7 +109,6 @@ int solve_dev_impl(eofa_ctx* ctx, const eofa_solve_params* prm, const double* b_
         if (info) *info = inf;
         return EOFA_OK;
     }
-    // initial guess
     if (P.use_x0) {
         launch_pack(ctx, P64, x_dev, x_e, x_o, st);
         if (P.system == EOFA_SYS_DWF) {  // iterate on y = D-tilde psi
@@ -135,81 +126,91 @@ int solve_dev_impl(eofa_ctx* ctx, const eofa_solve_params* prm, const double* b_
     const double fhn = std::sqrt(norm2_now(ctx, P64, fh, st));
 
     // inner work fields
-    Work w;
-    w.prec = prec;
-    w.precx = precx;
     const size_t fbi = field_bytes(prec, ctx->Vh, ctx->Ls);
     std::string tag = "_" + std::to_string(prec);
-    w.p = ctx_buffer(ctx, "sv_p" + tag, fbi);
-    w.q = ctx_buffer(ctx, "sv_q" + tag, fbi);
-    w.r = ctx_buffer(ctx, "sv_r" + tag, fbi);
-    w.s = ctx_buffer(ctx, "sv_s" + tag, fbi);
-    w.te = ctx_buffer(ctx, "sv_te" + tag, fbi);
-    w.te2 = ctx_buffer(ctx, "sv_te2" + tag, fbi);
-    w.to = ctx_buffer(ctx, "sv_to" + tag, fbi);
-    w.x = mixed ? ctx_buffer(ctx, "sv_x32", field_bytes(P32, ctx->Vh, ctx->Ls)) : x_o;
+    void* p = ctx_buffer(ctx, "sv_p" + tag, fbi);
+    void* q = ctx_buffer(ctx, "sv_q" + tag, fbi);
+    void* r = ctx_buffer(ctx, "sv_r" + tag, fbi);
+    void* s = ctx_buffer(ctx, "sv_s" + tag, fbi);
+    void* te = ctx_buffer(ctx, "sv_te" + tag, fbi);
+    void* to = ctx_buffer(ctx, "sv_to" + tag, fbi);
+    void* x = mixed ? ctx_buffer(ctx, "sv_x32", field_bytes(P32, ctx->Vh, ctx->Ls)) : x_o;
+    double* red = ctx->red;
 
     double target_rel = 0.5 * P.tol;  // on |r| / |f^|, refined by the true-residual check
     int restarts = 0;
     double true_rel = 1.0;
+    double hist[32];
     for (;;) {
         // r64 = f^ - A x_o  (FP64)
-        apply_A(ctx, ops, P64, x_o, r64, a_e, a_e2, st);
+        apply_A(ctx, ops, P64, x_o, r64, a_e, nullptr, 0, st);
         blas_axpby(ctx, P64, 1.0, fh, -1.0, r64, st);
         double rr = norm2_now(ctx, P64, r64, st);
         if (!is_finite(rr)) throw eofa_error(EOFA_ENUMERIC, "NaN/Inf in the residual");
-        double target = target_rel * fhn;
-        if (mixed) {
-            blas_copy(ctx, prec, w.r, P64, r64, st);
-            blas_zero(ctx, precx, w.x, st);
-        } else {
-            blas_copy(ctx, P64, w.r, P64, r64, st);
-        }
+        const double target = target_rel * fhn;
+        blas_copy(ctx, prec, r, P64, r64, st);
+        if (mixed) blas_zero(ctx, precx, x, st);
         double rmax = std::sqrt(rr);
+        int it = 0;  // iteration index within this CG run (parity of the gamma slots)
         if (std::sqrt(rr) > target) {
-            apply_Adag(ctx, ops, prec, w.r, w.s, w.te, w.te2, w.to, st);
-            blas_copy(ctx, prec, w.p, prec, w.s, st);
-            double gam = norm2_now(ctx, prec, w.s, st);
-            while (inf.iters < P.maxiter) {
-                apply_A(ctx, ops, prec, w.p, w.q, w.te, w.te2, st);
-                double dl = norm2_now(ctx, prec, w.q, st);
-                if (!is_finite(dl) || !is_finite(gam)) throw eofa_error(EOFA_ENUMERIC, "NaN/Inf in CG");
-                if (dl == 0.0) break;
-                double alpha = gam / dl;
-                blas_cg_update(ctx, prec, precx, alpha, w.p, w.q, w.x, w.r, 2, st);
-                apply_Adag(ctx, ops, prec, w.r, w.s, w.te, w.te2, w.to, st);
-                blas_norm2(ctx, prec, w.s, 4, st);
-                double vals[3];
-                red_fetch_many(ctx, 2, 3, vals, st);
-                rr = vals[0];
-                double gnew = vals[2];
-                inf.iters++;
+            // s = A^+ r, gamma -> slot of iteration 0, p = s
+            apply_Adag_cg(ctx, ops, prec, r, nullptr, 0, s, te, to, SC_RRH, SC_GAMMA, st);
+            blas_copy(ctx, prec, p, prec, s, st);
+            int chunk = 4;
+            double rr_prev = rr;
+            bool done = false;
+            while (!done && inf.iters < P.maxiter) {
+                int n = chunk;
+                if (n > P.maxiter - inf.iters) n = P.maxiter - inf.iters;
+                for (int k = 0; k < n; k++, it++) {
+                    apply_A(ctx, ops, prec, p, q, te, red, SC_DELTA, st);
+                    apply_Adag_cg(ctx, ops, prec, r, q, it, s, te, to, SC_RRH + (it & 31),
+                                  SC_GAMMA + ((it + 1) & 1), st);
+                    fused_xp_update(ctx, prec, precx, red, it, x, p, s, st);
+                }
+                inf.iters += n;
+                red_fetch_many(ctx, SC_RRH, 32, hist, st);
+                rr = hist[(it - 1) & 31];
                 if (!is_finite(rr)) throw eofa_error(EOFA_ENUMERIC, "NaN/Inf in CG");
-                if (mixed && (std::sqrt(rr) < delta * rmax || std::sqrt(rr) < target || inf.iters >= P.maxiter)) {
-                    // reliable update: accumulate x in FP64, recompute r in FP64
-                    blas_copy(ctx, P64, a_o, precx, w.x, st);
+                double rn = std::sqrt(rr);
+                bool want_update = mixed && (rn < delta * rmax || rn < target || inf.iters >= P.maxiter);
+                if (!mixed && rn < target) done = true;
+                if (want_update) {
+                    // reliable update: x64 += x, r64 = f^ - A x64 (FP64), r = r64, s = A^+ r
+                    blas_copy(ctx, P64, a_o, precx, x, st);
                     blas_axpby(ctx, P64, 1.0, a_o, 1.0, x_o, st);
-                    blas_zero(ctx, precx, w.x, st);
-                    apply_A(ctx, ops, P64, x_o, r64, a_e, a_e2, st);
+                    blas_zero(ctx, precx, x, st);
+                    apply_A(ctx, ops, P64, x_o, r64, a_e, nullptr, 0, st);
                     blas_axpby(ctx, P64, 1.0, fh, -1.0, r64, st);
                     rr = norm2_now(ctx, P64, r64, st);
                     inf.reliable_updates++;
-                    rmax = std::sqrt(rr);
-                    if (std::sqrt(rr) < target) break;
-                    blas_copy(ctx, prec, w.r, P64, r64, st);
-                    apply_Adag(ctx, ops, prec, w.r, w.s, w.te, w.te2, w.to, st);
-                    gnew = norm2_now(ctx, prec, w.s, st);
-                } else if (!mixed && std::sqrt(rr) < target) {
-                    break;
+                    rn = std::sqrt(rr);
+                    rmax = rn;
+                    if (rn < target || inf.iters >= P.maxiter) {
+                        done = true;
+                    } else {
+                        blas_copy(ctx, prec, r, P64, r64, st);
+                        apply_Adag_cg(ctx, ops, prec, r, nullptr, it, s, te, to, SC_RRH + ((it - 1) & 31),
+                                      SC_GAMMA + (it & 1), st);
+                    }
                 }
-                double beta = gnew / gam;
-                gam = gnew;
-                blas_axpby(ctx, prec, 1.0, w.s, beta, w.p, st);
+                // next chunk: iterations predicted to reach the next threshold
+                double thr = mixed ? std::max(delta * rmax, target) : target;
+                double rate = (rr_prev > 0 && rr < rr_prev && n > 0) ? std::pow(rr / rr_prev, 1.0 / n) : 0.0;
+                rr_prev = rr;
+                if (rate > 0 && rate < 1 && rr > thr * thr) {
+                    double need = std::log(thr * thr / rr) / std::log(rate);
+                    chunk = (int)std::ceil(need);
+                } else {
+                    chunk = 4;
+                }
+                if (chunk < 1) chunk = 1;
+                if (chunk > 32) chunk = 32;
             }
             if (mixed) {
-                blas_copy(ctx, P64, a_o, precx, w.x, st);
+                blas_copy(ctx, P64, a_o, precx, x, st);
                 blas_axpby(ctx, P64, 1.0, a_o, 1.0, x_o, st);
-                blas_zero(ctx, precx, w.x, st);
+                blas_zero(ctx, precx, x, st);
             }
         }
         // reconstruct psi_e = G'^{-1} (f_e - D_eo psi_o)
@@ -217,6 +218,10 @@ int solve_dev_impl(eofa_ctx* ctx, const eofa_solve_params* prm, const double* b_
         blas_axpby(ctx, P64, 1.0, f_e, -1.0, a_e, st);
         launch_op5(ctx, P64, ops.Gi, a_e, nullptr, x_e, st);
         // true residual of the full system
+        void* re = ctx_buffer(ctx, "sv_re", f64);
+        void* ro = ctx_buffer(ctx, "sv_ro", f64);
+        const void* out_e = x_e;
+        const void* out_o = x_o;
         if (P.system == EOFA_SYS_DWF) {
             // psi = D-tilde^{-1} y, residual b - D_DWF psi
             Op5 Dti = op_plain(S.c, 1, 0, 0);
@@ -224,31 +229,23 @@ int solve_dev_impl(eofa_ctx* ctx, const eofa_solve_params* prm, const double* b_
             void* po = ctx_buffer(ctx, "sv_po", f64);
             launch_op5(ctx, P64, Dti, x_e, nullptr, pe, st);
             launch_op5(ctx, P64, Dti, x_o, nullptr, po, st);
-            void* re = ctx_buffer(ctx, "sv_re", f64);
-            void* ro = ctx_buffer(ctx, "sv_ro", f64);
             apply_dwf_fields(ctx, S.c, 0, pe, po, re, ro, st);
-            blas_axpby(ctx, P64, 1.0, f_e, -1.0, re, st);
-            blas_axpby(ctx, P64, 1.0, f_o, -1.0, ro, st);
-            double res2 = norm2_now(ctx, P64, re, st) + norm2_now(ctx, P64, ro, st);
-            true_rel = std::sqrt(res2 / fnorm2);
-            if (true_rel <= P.tol || inf.iters >= P.maxiter || restarts >= 8 || !is_finite(true_rel)) {
-                launch_unpack(ctx, P64, pe, po, x_dev, st);
-                break;
-            }
+            out_e = pe;
+            out_o = po;
         } else {
-            void* re = ctx_buffer(ctx, "sv_re", f64);
-            void* ro = ctx_buffer(ctx, "sv_ro", f64);
             apply_eofa_fields(ctx, G, x_e, x_o, re, ro, st);
-            blas_axpby(ctx, P64, 1.0, f_e, -1.0, re, st);
-            blas_axpby(ctx, P64, 1.0, f_o, -1.0, ro, st);
-            double res2 = norm2_now(ctx, P64, re, st) + norm2_now(ctx, P64, ro, st);
-            true_rel = std::sqrt(res2 / fnorm2);
-            if (true_rel <= P.tol || inf.iters >= P.maxiter || restarts >= 8 || !is_finite(true_rel)) {
-                launch_unpack(ctx, P64, x_e, x_o, x_dev, st);
-                break;
-            }
+        }
+        blas_axpby(ctx, P64, 1.0, f_e, -1.0, re, st);
+        blas_axpby(ctx, P64, 1.0, f_o, -1.0, ro, st);
+        double res2 = norm2_now(ctx, P64, re, st) + norm2_now(ctx, P64, ro, st);
+        true_rel = std::sqrt(res2 / fnorm2);
+        if (true_rel <= P.tol || inf.iters >= P.maxiter || restarts >= 8 || !is_finite(true_rel)) {
+            launch_unpack(ctx, P64, out_e, out_o, x_dev, st);
+            break;
         }
         // not yet: tighten the inner target by the observed ratio and restart
+        apply_A(ctx, ops, P64, x_o, r64, a_e, nullptr, 0, st);
+        blas_axpby(ctx, P64, 1.0, fh, -1.0, r64, st);
         double rr_now = norm2_now(ctx, P64, r64, st);
         double ratio = std::sqrt(rr_now) / fhn / (true_rel > 0 ? true_rel : 1e-300);
         double nt = 0.5 * P.tol * ratio;

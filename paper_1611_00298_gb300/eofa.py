@@ -30,7 +30,7 @@ EXPORTS = [
     "eofa_solve", "eofa_solve_dev", "eofa_action", "eofa_action_dev", "eofa_force", "eofa_force_dev",
     "eofa_force_from_chi_dev", "eofa_grad_from_chi_dev", "eofa_coefficients", "eofa_link_update_dev",
     "eofa_solve_batched", "eofa_kernel_launches", "eofa_profile_start", "eofa_profile_stop",
-    "eofa_dwf_apply_noalloc",
+    "eofa_dwf_apply_noalloc", "eofa_schur_hop_dev",
 ]
 
 
@@ -84,6 +84,7 @@ def load_library(path: str = LIB_PATH):
         "eofa_eofa_apply_dev": (I, [P, I, D, D, D, P, P, P]),
         "eofa_field_bytes": (LL, [P, I]),
         "eofa_hop_dev": (I, [P, I, I, I, P, P, P]),
+        "eofa_schur_hop_dev": (I, [P, I, I, I, I, D, D, D, P, P, P]),
         "eofa_pack_dev": (I, [P, I, P, P, P, P]),
         "eofa_unpack_dev": (I, [P, I, P, P, P, P]),
         "eofa_solve": (I, [P, ctypes.POINTER(SolveParams), P, P, ctypes.POINTER(SolveInfo)]),
@@ -259,6 +260,11 @@ class Lattice:
     def hop_dev(self, precision, out_parity, dagger, inp, out):
         self._check(self.lib.eofa_hop_dev(self.ctx, precision, out_parity, int(dagger), _ptr(inp), _ptr(out),
                                           _stream()), "hop_dev")
+
+    def schur_hop_dev(self, precision, out_parity, dagger, inp, out, alpha, M5, mf):
+        """out = G^-1 D_hop in (dagger: G^-T D_hop^+ in), one fused kernel."""
+        self._check(self.lib.eofa_schur_hop_dev(self.ctx, precision, out_parity, int(dagger), self.Ls, alpha, M5, mf,
+                                                _ptr(inp), _ptr(out), _stream()), "schur_hop_dev")
 
     def pack_dev(self, precision, canon, even, odd):
         self._check(self.lib.eofa_pack_dev(self.ctx, precision, _ptr(canon), _ptr(even), _ptr(odd), _stream()),

@@ -123,3 +123,51 @@ def test_hop_kernel_each_precision(eofa, case, prec, tol):
             torch.cuda.synchronize()
             got = res.cpu().numpy()
             assert _rel(got, ref) < tol, (out_par, dag, _rel(got, ref))
+
+
+def _ginv_blocks(Ls, alpha, M5, mf):
+    """Dense per-chirality G^{-1} with G = (4 - M5) + D^perp, the 5D-local block of D_EOFA (Eq. (3))."""
+    Pp, Pm = dwf.dperp_matrices(Ls, alpha, mf)
+    one = np.eye(Ls)
+    return np.linalg.inv((4 - M5) * one + Pp), np.linalg.inv((4 - M5) * one + Pm)
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-12), (1, 2e-6), (2, 3e-3)])
+@pytest.mark.parametrize("case", [CASES[0], CASES[2], CASES[3], CASES[5], ((4, 4, 2, 2), 16, 2.0, 1.8, 0.1, -1),
+                                  ((2, 2, 2, 4), 24, 4.0, 1.8, 0.0362, -1)])
+def test_schur_hop_parity(eofa, case, prec, tol):
+    """Fused G^{-1} D_hop (and G^{-T} D_hop^+) against the oracle hop and dense 5D blocks."""
+    import torch
+    dims, Ls, alpha, M5, mf, bc = case
+    lat, U = _setup(eofa, dims, Ls, bc)
+    psi = inputs.fermion5d(dims, Ls, 6)
+    X, Y, Z, T = dims
+    t, z, y, x = np.meshgrid(*[np.arange(n) for n in (T, Z, Y, X)], indexing="ij")
+    par = (x + y + z + t) % 2
+    Gp, Gm = _ginv_blocks(Ls, alpha, M5, mf)
+    nb = lat.field_bytes(prec)
+    for out_par in (0, 1):
+        for dag in (0, 1):
+            src = psi * (par == 1 - out_par)[None, :, :, :, :, None, None]
+            hop = dwf.wilson_hop(U, src, bc, dagger=bool(dag))
+            if dag:
+                ref = dwf.apply_s(Gp.T, Gm.T, hop)
+            else:
+                ref = dwf.apply_s(Gp, Gm, hop)
+            ref = ref * (par == out_par)[None, :, :, :, :, None, None]
+            dev = torch.from_numpy(src.copy()).cuda()
+            ev = torch.empty(nb, dtype=torch.uint8, device="cuda")
+            od = torch.empty_like(ev)
+            out = torch.empty_like(ev)
+            zero = torch.zeros_like(ev)
+            lat.pack_dev(prec, dev, ev, od)
+            lat.pack_dev(prec, torch.zeros_like(dev), zero, zero)
+            lat.schur_hop_dev(prec, out_par, dag, od if out_par == 0 else ev, out, alpha, M5, mf)
+            res = torch.empty_like(dev)
+            if out_par == 0:
+                lat.unpack_dev(prec, out, zero, res)
+            else:
+                lat.unpack_dev(prec, zero, out, res)
+            torch.cuda.synchronize()
+            got = res.cpu().numpy()
+            assert _rel(got, ref) < tol, (out_par, dag, _rel(got, ref))
