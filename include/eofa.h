@@ -178,6 +178,27 @@ int eofa_grad_from_chi_dev(eofa_ctx* ctx, double k, const double* chiL_dev,
 int eofa_coefficients(int Ls, double alpha, double m1, double m2, double* k,
                       double* Omega_plus, double* Omega_minus);
 
+/* The two solves behind Eq. (5) and Eq. (7), into caller buffers:
+ * chi_L = H(m1)^{-1} Omega_- P_- phi, chi_R = [H(m2) - Delta_+ P_+]^{-1} Omega_+ P_+ phi
+ * (5D canonical, device); S (may be NULL) gets the action. */
+int eofa_pseudofermion_solutions_dev(eofa_ctx* ctx, int Ls, double alpha, double M5, double m1, double m2,
+                                     int precision, double tol, const double* phi_dev, double* chiL_dev,
+                                     double* chiR_dev, double* S, eofa_solve_info info[2], void* stream);
+
+/* Reliable-update threshold delta in (0, 1) used by the solves inside
+ * eofa_action / eofa_force / eofa_leapfrog_dev (default 0.1). */
+int eofa_set_reliable_delta(eofa_ctx* ctx, double delta);
+
+/* Leapfrog molecular-dynamics trajectory for H = sum_links tr P^2 + S_EOFA
+ * (Eq. (5), force Eq. (7)): P <- P - dtau/2 F, then nsteps times
+ * {U <- exp(i dtau P) U; P <- P - dtau F} with the last momentum step halved.
+ * P_dev (4 V traceless Hermitian 3x3, canonical) is updated in place; the
+ * context's gauge field and U_dev (canonical copy, may be NULL) end at the
+ * final links.  dH = H(end) - H(start); H0 (may be NULL) = H(start). */
+int eofa_leapfrog_dev(eofa_ctx* ctx, int Ls, double alpha, double M5, double m1, double m2, int precision,
+                      double tol, int nsteps, double dtau, const double* phi_dev, double* P_dev, double* U_dev,
+                      double* dH, double* H0, void* stream);
+
 /* Molecular dynamics link update U <- exp(i eps P) U on the device gauge
  * field of the context and on the canonical copy U_dev (if not NULL);
  * P: 4 V traceless Hermitian 3x3, canonical, device. */

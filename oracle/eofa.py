@@ -203,3 +203,39 @@ def leapfrog(U, P, phi, Ls, alpha, M5, m1, m2, bc_t, nsteps, dtau, tol=1e-12):
         P = P - (dtau if step < nsteps - 1 else 0.5 * dtau) * f
     H1 = kinetic(P) + action(U, phi, Ls, alpha, M5, m1, m2, bc_t, tol)
     return U, P, H1 - H0
+
+
+def force_at_link(U, chiL, chiR, k, bc_t, site, mu):
+    """F_mu(x) of Eq. (7) at one link (t, z, y, x) = site, from its definition.
+
+    Only chi at x and x + mu enter.  Plain loops over a = 1..8 and s; used to
+    check the force at sampled links of lattices too large for force_from_chi.
+    """
+    T = generators()
+    one = np.eye(4)
+    dims = U.shape[:4]
+    axis = {0: 3, 1: 2, 2: 1, 3: 0}[mu]  # position of mu in (t, z, y, x)
+    fwd = list(site)
+    fwd[axis] += 1
+    phase = 1.0
+    if fwd[axis] == dims[axis]:
+        fwd[axis] = 0
+        if mu == 3:
+            phase = bc_t
+    fwd = tuple(fwd)
+    Ls = chiL.shape[0]
+    Um = U[site + (mu,)]
+    F = np.zeros((3, 3), dtype=np.complex128)
+    for chi, sign in ((chiL, +1.0), (chiR, -1.0)):
+        for a in range(8):
+            dU = 1j * T[a] @ Um
+            val = 0.0j
+            for s in range(Ls):
+                zeta_x = dwf.GAMMA5 @ chi[Ls - 1 - s][site]          # (g5 R5 chi)(x, s)
+                zeta_f = dwf.GAMMA5 @ chi[Ls - 1 - s][fwd] * phase   # (g5 R5 chi)(x + mu, s), boundary phase
+                chi_f = chi[s][fwd] * phase
+                t1 = (one - dwf.GAMMA[mu]) @ (chi_f @ dU.T)           # (1 - g) dU chi(x + mu)
+                t2 = (one + dwf.GAMMA[mu]) @ (chi[s][site] @ np.conj(dU))  # (1 + g) dU^+ chi(x)
+                val += -0.5 * (np.vdot(zeta_x, t1) + np.vdot(zeta_f, t2))
+            F += sign * k * val.real * T[a]
+    return F

@@ -160,6 +160,7 @@ int eofa_create(eofa_ctx** out, const int dims[4], int Ls, int bc_t, int flags) 
     ctx->coef = ctx->red = ctx->red_host = nullptr;
     ctx->stream = nullptr;
     ctx->prof = nullptr;
+    ctx->rel_delta = 0.1;
     try {
         EOFA_CUDA(cudaGetDevice(&ctx->device));
         EOFA_CUDA(cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, ctx->device));
@@ -383,6 +384,12 @@ int eofa_eofa_apply(eofa_ctx* ctx, int Ls, double alpha, double M5, double mf, c
     if (!ctx || !in || !out) return fail(ctx, EOFA_EINVAL, "null argument");
     ApplyArgs a = {Ls, alpha, M5, mf, 0};
     return host_wrap_5d(ctx, in, out, eofa_thunk, &a);
+}
+
+int eofa_set_reliable_delta(eofa_ctx* ctx, double delta) {
+    if (!ctx || !(delta > 0 && delta < 1)) return fail(ctx, EOFA_EINVAL, "delta must lie in (0, 1)");
+    ctx->rel_delta = delta;
+    return EOFA_OK;
 }
 
 int eofa_coefficients(int Ls, double alpha, double m1, double m2, double* k, double* Omega_plus,

@@ -186,7 +186,8 @@ struct ChiBufs {
 
 // The two solves behind Eq. (5) and Eq. (7); fills S if requested.
 ChiBufs eofa_chis(eofa_ctx* ctx, int Ls, double alpha, double M5, double m1, double m2, int precision, double tol,
-                  const double* phi_dev, double* S, eofa_solve_info info[2], cudaStream_t st, int* rc_out) {
+                  const double* phi_dev, double* S, eofa_solve_info info[2], cudaStream_t st, int* rc_out,
+                  double* chiL_out = nullptr, double* chiR_out = nullptr) {
     check_ls(ctx, Ls);
     require_gauge(ctx);
     if (!(m1 < m2)) throw eofa_error(EOFA_EINVAL, "EOFA needs m1 < m2 (k > 0)");
@@ -195,8 +196,8 @@ ChiBufs eofa_chis(eofa_ctx* ctx, int Ls, double alpha, double M5, double m1, dou
     ChiBufs c;
     c.bL = (double*)ctx_buffer(ctx, "eo_bL", b5);
     c.bR = (double*)ctx_buffer(ctx, "eo_bR", b5);
-    c.chiL = (double*)ctx_buffer(ctx, "eo_chiL", b5);
-    c.chiR = (double*)ctx_buffer(ctx, "eo_chiR", b5);
+    c.chiL = chiL_out ? chiL_out : (double*)ctx_buffer(ctx, "eo_chiL", b5);
+    c.chiR = chiR_out ? chiR_out : (double*)ctx_buffer(ctx, "eo_chiR", b5);
     double* om = (double*)ctx_buffer(ctx, "eo_omega", 2 * EOFA_MAX_LS * sizeof(double));
     std::vector<double> Op(Ls), Om(Ls);
     eofa_omega(Ls, alpha, Op.data(), Om.data());
@@ -217,7 +218,7 @@ ChiBufs eofa_chis(eofa_ctx* ctx, int Ls, double alpha, double M5, double m1, dou
     p.precision = precision;
     p.tol = tol;
     p.maxiter = 100000;
-    p.delta = 0.1;
+    p.delta = ctx->rel_delta;
     p.use_x0 = 0;
     p.system = EOFA_SYS_EOFA_L;
     p.shift = 0.0;
@@ -239,6 +240,14 @@ ChiBufs eofa_chis(eofa_ctx* ctx, int Ls, double alpha, double M5, double m1, dou
 }
 
 }  // namespace
+
+int eofa_chis_to(eofa_ctx* ctx, int Ls, double alpha, double M5, double m1, double m2, int precision, double tol,
+                 const double* phi_dev, double* chiL, double* chiR, double* S, eofa_solve_info info[2], cudaStream_t st) {
+    int rc = EOFA_OK;
+    eofa_chis(ctx, Ls, alpha, M5, m1, m2, precision, tol, phi_dev, S, info, st, &rc, chiL, chiR);
+    EOFA_CUDA(cudaStreamSynchronize(st));
+    return rc;
+}
 
 extern "C" {
 

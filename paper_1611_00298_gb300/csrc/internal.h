@@ -121,6 +121,7 @@ struct eofa_ctx {
     std::map<std::string, void*> bufs;  // named workspace fields
     std::map<std::string, size_t> buf_sizes;
     Prof* prof;
+    double rel_delta;  // reliable-update threshold of the solves inside action / force / MD
 };
 
 // ------------------------------------------------------------------ helpers

@@ -1,0 +1,42 @@
+// Solver state shared by single and batched solves (solver.cu, batch.cu).
+#pragma once
+#include "api_util.h"
+#include "fused.h"
+
+// One even-odd CGLS solve of (D_hop + G') psi = f (see solver.cu).  The
+// iteration kernels read and write only this object's reduction scratch
+// `red`, so several solves can run concurrently on one context.
+struct Solve {
+    eofa_ctx* ctx;
+    eofa_solve_params P;
+    int prec, precx;
+    bool mixed;
+    double delta;
+    System5 S;
+    Op5 Gi, GiT, G;
+    double* red;       // reduction scratch / device scalars of this solve
+    std::string tag;   // buffer-name suffix
+    // FP64 half fields
+    void *f_e, *f_o, *fh, *x_e, *x_o, *r64, *a_e, *a_o;
+    // inner-precision fields
+    void *p, *q, *r, *s, *te, *to, *x;
+    double fnorm2, fhn, rmax, target_rel, target, true_rel;
+    int it, ring, restarts;
+    bool done, trivial;
+    eofa_solve_info inf;
+
+    // b_dev, x_dev: canonical 5D device fields (x_dev holds x0 when P.use_x0)
+    void setup(eofa_ctx* c, const eofa_solve_params& p, const double* b_dev, const double* x_dev, const std::string& tg,
+               double* red_scratch, int ring_len, cudaStream_t st);
+    // start a CG run from the current FP64 iterate x_o; returns false if already converged
+    bool start_cg(cudaStream_t st);
+    // queue n CG iterations (no host synchronisation)
+    void enqueue(int n, cudaStream_t st);
+    // after a queued chunk: read |r|^2, do a reliable update if due; sets done when the inner target is met
+    void check(int n, cudaStream_t st);
+    // fold the inner solution into x_o, reconstruct, compute the true residual; true when finished
+    bool finish(double* x_dev, cudaStream_t st);
+};
+
+int solve_dev_impl(eofa_ctx* ctx, const eofa_solve_params* p, const double* b_dev, double* x_dev,
+                   eofa_solve_info* info, cudaStream_t st);

@@ -30,7 +30,8 @@ EXPORTS = [
     "eofa_solve", "eofa_solve_dev", "eofa_action", "eofa_action_dev", "eofa_force", "eofa_force_dev",
     "eofa_force_from_chi_dev", "eofa_grad_from_chi_dev", "eofa_coefficients", "eofa_link_update_dev",
     "eofa_solve_batched", "eofa_kernel_launches", "eofa_profile_start", "eofa_profile_stop",
-    "eofa_dwf_apply_noalloc", "eofa_schur_hop_dev",
+    "eofa_dwf_apply_noalloc", "eofa_schur_hop_dev", "eofa_pseudofermion_solutions_dev",
+    "eofa_set_reliable_delta", "eofa_leapfrog_dev",
 ]
 
 
@@ -101,6 +102,10 @@ def load_library(path: str = LIB_PATH):
                                    ctypes.POINTER(P), ctypes.POINTER(SolveInfo)]),
         "eofa_kernel_launches": (LL, []),
         "eofa_dwf_apply_noalloc": (I, [P, I, D, D, D, I, P, P, P]),
+        "eofa_pseudofermion_solutions_dev": (I, [P, I, D, D, D, D, I, D, P, P, P, ctypes.POINTER(D),
+                                                 ctypes.POINTER(SolveInfo), P]),
+        "eofa_set_reliable_delta": (I, [P, D]),
+        "eofa_leapfrog_dev": (I, [P, I, D, D, D, D, I, D, I, D, P, P, P, ctypes.POINTER(D), ctypes.POINTER(D), P]),
         "eofa_profile_start": (I, [P]),
         "eofa_profile_stop": (I, [P, ctypes.POINTER(Profile)]),
     }
@@ -322,6 +327,28 @@ class Lattice:
         pr = Profile()
         self._check(self.lib.eofa_profile_stop(self.ctx, ctypes.byref(pr)), "profile_stop")
         return list(pr.launches), list(pr.ms)
+
+    def pseudofermion_solutions_dev(self, phi, chiL, chiR, alpha, M5, m1, m2, precision=PREC_F64, tol=1e-10):
+        """chi_L, chi_R of Eq. (5) / (7) into the given device tensors; returns (S, info)."""
+        S = ctypes.c_double()
+        info = (SolveInfo * 2)()
+        rc = self.lib.eofa_pseudofermion_solutions_dev(self.ctx, self.Ls, alpha, M5, m1, m2, precision, tol, _ptr(phi),
+                                                       _ptr(chiL), _ptr(chiR), ctypes.byref(S), info, _stream())
+        self._check(rc, "pseudofermion_solutions_dev")
+        return S.value, info
+
+    def set_reliable_delta(self, delta):
+        self._check(self.lib.eofa_set_reliable_delta(self.ctx, delta), "set_reliable_delta")
+
+    def leapfrog_dev(self, phi, P, U, alpha, M5, m1, m2, nsteps, dtau, precision=PREC_F64, tol=1e-10):
+        """Leapfrog trajectory (P, U updated in place on the device); returns (dH, H0)."""
+        dH = ctypes.c_double()
+        H0 = ctypes.c_double()
+        rc = self.lib.eofa_leapfrog_dev(self.ctx, self.Ls, alpha, M5, m1, m2, precision, tol, nsteps, dtau, _ptr(phi),
+                                        _ptr(P), _ptr(U) if U is not None else None, ctypes.byref(dH),
+                                        ctypes.byref(H0), _stream())
+        self._check(rc, "leapfrog_dev")
+        return dH.value, H0.value
 
     def link_update_dev(self, eps, P, U=None):
         self._check(self.lib.eofa_link_update_dev(self.ctx, eps, _ptr(P), _ptr(U) if U is not None else None,
