@@ -202,3 +202,34 @@ def deofa(U, psi, alpha, M5, mf, bc_t):
 def hermitian_H(U, psi, alpha, M5, mf, bc_t):
     """H(m) = gamma_5 R_5 D_EOFA(m) (Sec. 2, after Eq. (4))."""
     return gamma5(R5(deofa(U, psi, alpha, M5, mf, bc_t)))
+
+
+def wilson_hop_at(U, psi, site, s, bc_t, dagger=False):
+    """The hopping part of D_w at one output site (t, z, y, x) = site and slice s.
+
+    Same definition as wilson_hop, evaluated from the eight neighbours only,
+    for checking kernels on lattices too large for whole-field numpy.
+    """
+    sgn = -1.0 if dagger else 1.0
+    dims = U.shape[:4]
+    one = np.eye(4)
+    out = np.zeros((4, 3), dtype=np.complex128)
+    for mu in range(4):
+        axis = {0: 3, 1: 2, 2: 1, 3: 0}[mu]
+        fwd, bwd = list(site), list(site)
+        fwd[axis] += 1
+        bwd[axis] -= 1
+        pf = pb = 1.0
+        if fwd[axis] == dims[axis]:
+            fwd[axis] = 0
+            pf = bc_t if mu == 3 else 1.0
+        if bwd[axis] < 0:
+            bwd[axis] = dims[axis] - 1
+            pb = bc_t if mu == 3 else 1.0
+        fwd, bwd = tuple(fwd), tuple(bwd)
+        Uf = U[site + (mu,)]
+        Ub = U[bwd + (mu,)]
+        vf = pf * (psi[s][fwd] @ Uf.T)                 # U_mu(x) psi(x + mu), colour on the right index
+        vb = pb * (psi[s][bwd] @ np.conj(Ub))          # U_mu(x - mu)^+ psi(x - mu)
+        out -= 0.5 * ((one - sgn * GAMMA[mu]) @ vf + (one + sgn * GAMMA[mu]) @ vb)
+    return out

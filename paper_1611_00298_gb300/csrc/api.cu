@@ -160,7 +160,8 @@ int eofa_create(eofa_ctx** out, const int dims[4], int Ls, int bc_t, int flags) 
     ctx->coef = ctx->red = ctx->red_host = nullptr;
     ctx->stream = nullptr;
     ctx->prof = nullptr;
-    ctx->rel_delta = 0.1;
+    ctx->tuned = new std::map<long long, int>();
+    ctx->rel_delta = 0.0;  // precision default
     try {
         EOFA_CUDA(cudaGetDevice(&ctx->device));
         EOFA_CUDA(cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, ctx->device));
@@ -170,7 +171,7 @@ int eofa_create(eofa_ctx** out, const int dims[4], int Ls, int bc_t, int flags) 
         ctx->nbr = (int*)ctx_buffer(ctx, "nbr", nb.size() * sizeof(int));
         EOFA_CUDA(cudaMemcpy(ctx->nbr, nb.data(), nb.size() * sizeof(int), cudaMemcpyHostToDevice));
         ctx->gauge[P64] = ctx_buffer(ctx, "gauge64", (size_t)V * 4 * 9 * 16);
-        ctx->gauge[P32] = ctx_buffer(ctx, "gauge32", (size_t)V * 4 * 9 * 8);
+        ctx->gauge[P32] = ctx_buffer(ctx, "gauge32", (size_t)V * 4 * 10 * 8);
         ctx->gauge[P16] = ctx->gauge[P32];
         ctx->coef = (double*)ctx_buffer(ctx, "coef", 16 * EOFA_MAX_LS * sizeof(double));
         ctx->red = (double*)ctx_buffer(ctx, "red", red_scratch_bytes());
@@ -195,6 +196,7 @@ int eofa_destroy(eofa_ctx* ctx) {
         for (auto& e : ctx->prof->ev) cudaEventDestroy(e);
         delete ctx->prof;
     }
+    delete ctx->tuned;
     delete ctx;
     return EOFA_OK;
 }
@@ -387,7 +389,7 @@ int eofa_eofa_apply(eofa_ctx* ctx, int Ls, double alpha, double M5, double mf, c
 }
 
 int eofa_set_reliable_delta(eofa_ctx* ctx, double delta) {
-    if (!ctx || !(delta > 0 && delta < 1)) return fail(ctx, EOFA_EINVAL, "delta must lie in (0, 1)");
+    if (!ctx || !(delta >= 0 && delta < 1)) return fail(ctx, EOFA_EINVAL, "delta must lie in [0, 1)");
     ctx->rel_delta = delta;
     return EOFA_OK;
 }

@@ -21,6 +21,15 @@
 #include "field.cuh"
 #include "fused.h"
 
+// minimum resident blocks of 256 threads per SM requested from the register
+// allocator (3 -> at most 85 registers, 8 blocks of 96 threads per SM)
+#ifndef EOFA_DSLASH_MINB
+#define EOFA_DSLASH_MINB 3
+#endif
+#ifndef EOFA_HOP_MINB
+#define EOFA_HOP_MINB 3
+#endif
+
 namespace dsl {
 namespace {
 
@@ -37,43 +46,65 @@ __device__ __forceinline__ void apply_A(const cpx<R>* l0, const cpx<R>* l1, cpx<
     }
 }
 
-// acc += (1 + SG gamma_mu) V psi (V = U or U^+), negated when neg.  The two
-// half-spinor rows are handled one after the other to keep few registers
-// live: row k contributes V h_k to acc[3k..3k+2] and SG (A^+ (V h))_k to the
-// lower spins.
+// One SU(3) row (3 complex) of a link: row a of U, or row a of U^+ (the
+// conjugated column a of U).
+template <typename R>
+__device__ __forceinline__ void link_row(const void* g, long long idx, int a, bool dag, cpx<R>* r);
+
+template <>
+__device__ __forceinline__ void link_row<double>(const void* g, long long idx, int a, bool dag, cpx<double>* r) {
+    const double2* b = (const double2*)g + idx * 9;
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        double2 t = __ldg(b + (dag ? 3 * k + a : 3 * a + k));
+        r[k] = dag ? mk(t.x, -t.y) : mk(t.x, t.y);
+    }
+}
+
+template <>
+__device__ __forceinline__ void link_row<float>(const void* g, long long idx, int a, bool dag, cpx<float>* r) {
+    const float2* b = (const float2*)g + idx * 10;
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        float2 t = __ldg(b + (dag ? 3 * k + a : 3 * a + k));
+        r[k] = dag ? mk(t.x, -t.y) : mk(t.x, t.y);
+    }
+}
+
+// acc += (1 + SG gamma_mu) V psi (V = U or U^+), negated when neg.  Few
+// registers stay live: the two half-spinor rows h0, h1 are formed first,
+// then the link is read one row at a time; row a gives component a of
+// W_k = V h_k, which adds to the upper spins and, through A^+, to the lower.
 template <int MU, int SG, bool DAGLINK, typename R>
-__device__ __forceinline__ void hop_dir(const cpx<R>* psi, const Link<R>& U, bool neg, cpx<R>* acc) {
-    cpx<R> a0[3], a1[3];
+__device__ __forceinline__ void hop_dir(const cpx<R>* psi, const void* gauge, long long lidx, bool neg,
+                                        cpx<R>* acc) {
+    cpx<R> a0[3], a1[3], h0[3], h1[3];
     apply_A<MU>(psi + 6, psi + 9, a0, a1);
 #pragma unroll
-    for (int row = 0; row < 2; row++) {
-        cpx<R> h[3], w[3];
-#pragma unroll
-        for (int c = 0; c < 3; c++) {
-            cpx<R> a = row == 0 ? a0[c] : a1[c];
-            cpx<R> v = psi[3 * row + c];
-            h[c] = SG > 0 ? v + a : v - a;
-            if (neg) h[c] = mk(-h[c].re, -h[c].im);
+    for (int c = 0; c < 3; c++) {
+        h0[c] = SG > 0 ? psi[c] + a0[c] : psi[c] - a0[c];
+        h1[c] = SG > 0 ? psi[3 + c] + a1[c] : psi[3 + c] - a1[c];
+        if (neg) {
+            h0[c] = mk(-h0[c].re, -h0[c].im);
+            h1[c] = mk(-h1[c].re, -h1[c].im);
         }
+    }
 #pragma unroll
-        for (int a = 0; a < 3; a++) {
-            if (DAGLINK) w[a] = cjmul(U.m[a], h[0]) + cjmul(U.m[3 + a], h[1]) + cjmul(U.m[6 + a], h[2]);
-            else w[a] = cmul(U.m[3 * a], h[0]) + cmul(U.m[3 * a + 1], h[1]) + cmul(U.m[3 * a + 2], h[2]);
-        }
-        // upper spin `row`
-#pragma unroll
-        for (int c = 0; c < 3; c++) acc[3 * row + c] = acc[3 * row + c] + w[c];
-        // lower spins: (A^+ W)_0 and (A^+ W)_1 in terms of W_row
-#pragma unroll
-        for (int c = 0; c < 3; c++) {
-            cpx<R> t;
-            int dst;
-            if (MU == 0) { t = itimes(w[c]); dst = row == 0 ? 9 : 6; }               // (iW1, iW0)
-            else if (MU == 1) { t = row == 0 ? mk(-w[c].re, -w[c].im) : w[c]; dst = row == 0 ? 9 : 6; }  // (W1, -W0)
-            else if (MU == 2) { t = row == 0 ? itimes(w[c]) : mitimes(w[c]); dst = row == 0 ? 6 : 9; }   // (iW0, -iW1)
-            else { t = w[c]; dst = row == 0 ? 6 : 9; }                                  // (W0, W1)
-            acc[dst + c] = SG > 0 ? acc[dst + c] + t : acc[dst + c] - t;
-        }
+    for (int a = 0; a < 3; a++) {
+        cpx<R> u[3];
+        link_row<R>(gauge, lidx, a, DAGLINK, u);
+        const cpx<R> w0 = cmul(u[0], h0[0]) + cmul(u[1], h0[1]) + cmul(u[2], h0[2]);
+        const cpx<R> w1 = cmul(u[0], h1[0]) + cmul(u[1], h1[1]) + cmul(u[2], h1[2]);
+        acc[a] = acc[a] + w0;
+        acc[3 + a] = acc[3 + a] + w1;
+        // lower spins: SG (A^+ W)
+        cpx<R> l0, l1;
+        if (MU == 0) { l0 = itimes(w1); l1 = itimes(w0); }
+        else if (MU == 1) { l0 = w1; l1 = mk(-w0.re, -w0.im); }
+        else if (MU == 2) { l0 = itimes(w0); l1 = mitimes(w1); }
+        else { l0 = w0; l1 = w1; }
+        acc[6 + a] = SG > 0 ? acc[6 + a] + l0 : acc[6 + a] - l0;
+        acc[9 + a] = SG > 0 ? acc[9 + a] + l1 : acc[9 + a] - l1;
     }
 }
 
@@ -82,17 +113,14 @@ __device__ __forceinline__ void hop_mu(const Geom& g, int par, int j, int s, int
                                        const void* gauge, cpx<typename Field<P>::R>* acc) {
     typedef typename Field<P>::R R;
     cpx<R> psi[12];
-    Link<R> U;
     const int* nb = par ? g.nbr[1] : g.nbr[0];
     int e = __ldg(nb + (2 * MU) * g.Vh + j);
     Field<P>::load(in, e & 0x7fffffff, s, Ls, n5, psi);
-    load_link<R>(gauge, (long long)((par * 4 + MU) * g.Vh + j), U);
-    hop_dir<MU, DAG ? 1 : -1, false>(psi, U, e < 0, acc);
+    hop_dir<MU, DAG ? 1 : -1, false>(psi, gauge, (long long)((par * 4 + MU) * g.Vh + j), e < 0, acc);
     e = __ldg(nb + (2 * MU + 1) * g.Vh + j);
     const int jn = e & 0x7fffffff;
     Field<P>::load(in, jn, s, Ls, n5, psi);
-    load_link<R>(gauge, (long long)(((1 - par) * 4 + MU) * g.Vh + jn), U);
-    hop_dir<MU, DAG ? -1 : 1, true>(psi, U, e < 0, acc);
+    hop_dir<MU, DAG ? -1 : 1, true>(psi, gauge, (long long)(((1 - par) * 4 + MU) * g.Vh + jn), e < 0, acc);
 }
 
 // ---------------------------------------------------------------- 5D-local column ops
@@ -325,10 +353,12 @@ __device__ __forceinline__ double cg_beta(const double* sc, int it) {
 
 // ---------------------------------------------------------------- fused dslash
 
-template <int P, int DAG, int LS>
-__global__ void __launch_bounds__(256, 3) dslash_kernel(Geom g, int par, const void* __restrict__ in, void* out,
-                                                     const void* __restrict__ gauge, Op5 op, const void* y,
-                                                     double a_out, double b_in, double* red, int slot, int NS) {
+// HASOP = false: B is the identity (plain hop), compiled separately so that
+// the register budget of the hop is not set by the 5D-local recurrences.
+template <int P, int DAG, int LS, bool HASOP>
+__global__ void __launch_bounds__(256, HASOP ? EOFA_DSLASH_MINB : EOFA_HOP_MINB) dslash_kernel(
+    Geom g, int par, const void* __restrict__ in, void* out, const void* __restrict__ gauge, Op5 op, const void* y,
+    double a_out, double b_in, double* red, int slot, int NS) {
     typedef typename Field<P>::R R;
     extern __shared__ __align__(16) unsigned char smraw[];
     cpx<R>* sm = reinterpret_cast<cpx<R>*>(smraw);
@@ -337,7 +367,7 @@ __global__ void __launch_bounds__(256, 3) dslash_kernel(Geom g, int par, const v
     const long long n5 = (long long)g.Vh * Ls;
     const int ls = threadIdx.x / Ls, s = threadIdx.x - ls * Ls;
     const bool active_thread = ls < NS;
-    const bool ident = op_is_identity(op);
+    const bool ident = !HASOP;
     const int ntiles = (g.Vh + NS - 1) / NS;
     const R scale = (R)(-0.5 * a_out);
     double nacc = 0.0;
@@ -499,20 +529,73 @@ unsigned grid_size(K kernel, int threads, size_t smem, int ntiles, int sms) {
     return (unsigned)(ntiles < cap ? (ntiles > 0 ? ntiles : 1) : cap);
 }
 
+// Autotuner: the sites per tile (NS) of the fused dslash are timed once per
+// context and kernel variant, with CUDA events on the launching stream, over
+// the heuristic choice and its halving / doubling.  The kernel is
+// idempotent (it only writes out and the reduction scratch), so the trial
+// launches are harmless.  Small lattices, and launches during stream capture,
+// use the heuristic.
+template <typename K>
+void launch_with(K k, const eofa_ctx* ctx, const Geom& g, int NS, size_t elem, bool hasop, int par, const void* in,
+                 void* out, const void* gauge, const Op5& op, const void* y, double a_out, double b_in, double* red,
+                 int slot, cudaStream_t st) {
+    const int threads = (NS * g.Ls + 31) / 32 * 32;
+    const size_t smem = hasop ? (size_t)NS * 12 * (g.Ls + 1) * elem : 0;
+    const int ntiles = (g.Vh + NS - 1) / NS;
+    if (smem > 40 * 1024) EOFA_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    unsigned grid = grid_size(k, threads, smem, ntiles, ctx->sms);
+    k<<<grid, threads, smem, st>>>(g, par, in, out, gauge, op, y, a_out, b_in, red, slot, NS);
+}
+
+template <typename K>
+int tuned_ns(K k, const eofa_ctx* ctx, const Geom& g, long long key, int ns0, size_t elem, bool hasop, int par,
+             const void* in, void* out, const void* gauge, const Op5& op, const void* y, double a_out, double b_in,
+             double* red, int slot, cudaStream_t st) {
+    auto it = ctx->tuned->find(key);
+    if (it != ctx->tuned->end()) return it->second;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    EOFA_CUDA(cudaStreamIsCapturing(st, &cs));
+    if (cs != cudaStreamCaptureStatusNone || (long long)g.Vh * g.Ls < (1LL << 20)) return ns0;
+    int cand[3] = {ns0 / 2, ns0, ns0 * 2};
+    int best = ns0;
+    float best_ms = 1e30f;
+    cudaEvent_t e0, e1;
+    EOFA_CUDA(cudaEventCreate(&e0));
+    EOFA_CUDA(cudaEventCreate(&e1));
+    for (int c : cand) {
+        if (c < 1 || c * g.Ls > 512 || (hasop && (size_t)c * 12 * (g.Ls + 1) * elem > 64 * 1024)) continue;
+        launch_with(k, ctx, g, c, elem, hasop, par, in, out, gauge, op, y, a_out, b_in, red, slot, st);  // warm
+        EOFA_CUDA(cudaEventRecord(e0, st));
+        for (int r = 0; r < 3; r++)
+            launch_with(k, ctx, g, c, elem, hasop, par, in, out, gauge, op, y, a_out, b_in, red, slot, st);
+        EOFA_CUDA(cudaEventRecord(e1, st));
+        EOFA_CUDA(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        EOFA_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = c;
+        }
+    }
+    EOFA_CUDA(cudaEventDestroy(e0));
+    EOFA_CUDA(cudaEventDestroy(e1));
+    EOFA_CUDA(cudaGetLastError());
+    (*ctx->tuned)[key] = best;
+    return best;
+}
+
 template <int P, int DAG, int LS>
 void launch_dslash_t(const eofa_ctx* ctx, int par, const void* in, void* out, const Op5& op, const void* y,
                      double a_out, double b_in, double* red, int slot, cudaStream_t st) {
     typedef typename Field<P>::R R;
     Geom g = ctx_geom(ctx);
-    const int NS = pick_ns(g.Ls, sizeof(cpx<R>));
-    const int threads = (NS * g.Ls + 31) / 32 * 32;
-    const size_t smem = (size_t)NS * 12 * (g.Ls + 1) * sizeof(cpx<R>);
-    const int ntiles = (g.Vh + NS - 1) / NS;
     const void* gauge = ctx->gauge[P == P64 ? P64 : P32];
-    auto k = dslash_kernel<P, DAG, LS>;
-    if (smem > 40 * 1024) EOFA_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    unsigned grid = grid_size(k, threads, smem, ntiles, ctx->sms);
-    k<<<grid, threads, smem, st>>>(g, par, in, out, gauge, op, y, a_out, b_in, red, slot, NS);
+    const bool hasop = op.inv[0] || op.inv[1] || op.fwd[0] || op.fwd[1] || op.sigma[0] != 0.0 || op.sigma[1] != 0.0;
+    auto k = hasop ? dslash_kernel<P, DAG, LS, true> : dslash_kernel<P, DAG, LS, false>;
+    const long long key = ((((long long)P * 2 + DAG) * 128 + g.Ls) * 2 + (hasop ? 1 : 0)) * 2 + (y ? 1 : 0);
+    const int NS = tuned_ns(k, ctx, g, key, pick_ns(g.Ls, sizeof(cpx<R>)), sizeof(cpx<R>), hasop, par, in, out, gauge,
+                            op, y, a_out, b_in, red, slot, st);
+    launch_with(k, ctx, g, NS, sizeof(cpx<R>), hasop, par, in, out, gauge, op, y, a_out, b_in, red, slot, st);
     EOFA_LAUNCHED();
 }
 

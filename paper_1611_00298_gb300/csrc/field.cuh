@@ -114,12 +114,16 @@ __device__ __forceinline__ void load_link<double>(const void* g, long long idx, 
     }
 }
 
+// FP32 links are padded to 10 complex (80 bytes) and read as five float4
 template <>
 __device__ __forceinline__ void load_link<float>(const void* g, long long idx, Link<float>& L) {
-    const float2* b = (const float2*)g + idx * 9;
+    const float4* b = (const float4*)g + idx * 5;
 #pragma unroll
-    for (int k = 0; k < 9; k++) {
-        float2 t = __ldg(b + k);
-        L.m[k] = mk(t.x, t.y);
+    for (int k = 0; k < 4; k++) {
+        float4 t = __ldg(b + k);
+        L.m[2 * k] = mk(t.x, t.y);
+        L.m[2 * k + 1] = mk(t.z, t.w);
     }
+    float4 t = __ldg(b + 4);
+    L.m[8] = mk(t.x, t.y);
 }

@@ -50,8 +50,9 @@ __host__ __device__ __forceinline__ cpx<R> mitimes(cpx<R> a) { return mk(a.im, -
 //   FP32: chunk k = components 2k, 2k + 1  -> [j][6][Ls]  float4
 //   FP16: chunk k = components 4k .. 4k+3  -> [j][3][Ls]  8 x half, plus a
 //         per-site FP32 scale [j][Ls] stored after the chunks.
-// Gauge field (per precision): [parity][mu][j][9] complex (row-major 3x3),
-// forward links U_mu(x) of the sites of that parity.
+// Gauge field (per precision): [parity][mu][j][3x3] complex (row-major),
+// forward links U_mu(x) of the sites of that parity; FP64 links take 9
+// complex, FP32 links are padded to 10 complex (80 bytes, 16-byte aligned).
 
 enum Prec { P64 = 0, P32 = 1, P16 = 2 };
 
@@ -121,6 +122,7 @@ struct eofa_ctx {
     std::map<std::string, void*> bufs;  // named workspace fields
     std::map<std::string, size_t> buf_sizes;
     Prof* prof;
+    std::map<long long, int>* tuned;  // autotuned sites-per-tile of the fused dslash, by kernel key
     double rel_delta;  // reliable-update threshold of the solves inside action / force / MD
 };
 

@@ -64,8 +64,9 @@ __global__ void gauge_pack_kernel(Geom g, const double* __restrict__ canon, doub
     for (int k = 0; k < 9; k++) {
         double2 z = src[k];
         g64[tid * 9 + k] = z;
-        g32[tid * 9 + k] = make_float2((float)z.x, (float)z.y);
+        g32[tid * 10 + k] = make_float2((float)z.x, (float)z.y);
     }
+    g32[tid * 10 + 9] = make_float2(0.f, 0.f);  // pad: 80-byte links, five 16-byte loads
 }
 
 // max over links of |U^+ U - 1|_max, via atomicMax on the bit pattern (values >= 0)

@@ -77,7 +77,11 @@ void Solve::setup(eofa_ctx* c, const eofa_solve_params& prm, const double* b_dev
     mixed = P.precision != EOFA_PREC_F64;
     prec = P.precision == EOFA_PREC_F64 ? P64 : (P.precision == EOFA_PREC_MIXED_F32 ? P32 : P16);
     precx = mixed ? P32 : P64;
-    delta = (P.delta > 0 && P.delta < 1) ? P.delta : 0.1;
+    // reliable-update threshold: delta <= 0 picks the default of the inner
+    // precision; FP16 storage cannot follow the residual down more than ~1e-2
+    const double auto_delta = prec == P16 ? 0.1 : 1e-3;
+    delta = (P.delta > 0 && P.delta < 1) ? P.delta : auto_delta;
+    if (prec == P16 && delta < 0.05) delta = 0.05;
     S = P.system == EOFA_SYS_DWF ? system_dwf(P.alpha, P.M5, P.mf)
                                  : system_eofa(P.Ls, P.alpha, P.M5, P.m1, P.m2, P.system, P.shift);
     // per-solve coefficient slots so that concurrent solves on one context do not clash
@@ -187,7 +191,10 @@ void Solve::check(int n, cudaStream_t st) {
         if (rn < target || inf.iters >= P.maxiter) done = true;
         return;
     }
-    if (rn < delta * rmax || rn < target || inf.iters >= P.maxiter) {
+    // a residual above the last recomputed one means the low-precision recursion
+    // has lost track: recompute in FP64 and restart the search direction
+    const bool diverging = rn > rmax;
+    if (rn < delta * rmax || rn < target || inf.iters >= P.maxiter || diverging) {
         // reliable update: x64 += x, r64 = f^ - A x64 (FP64), r = r64, s = A^+ r
         blas_copy(ctx, P64, a_o, precx, x, st);
         blas_axpby(ctx, P64, 1.0, a_o, 1.0, x_o, st);
@@ -204,6 +211,7 @@ void Solve::check(int n, cudaStream_t st) {
             blas_copy(ctx, prec, r, P64, r64, st);
             apply_Adag_cg(ctx, GiT, prec, r, nullptr, red, it, s, te, to, SC_RRH + ((it + ring - 1) % ring),
                           SC_GAMMA + (it & 1), st);
+            if (diverging) blas_copy(ctx, prec, p, prec, s, st);
         }
     }
 }

@@ -225,7 +225,7 @@ class Lattice:
         return out
 
     def solve_params(self, system=SYS_DWF, alpha=2.0, M5=1.8, mf=0.0, m1=0.0, m2=0.0, shift=0.0,
-                     precision=PREC_F64, tol=1e-10, maxiter=100000, delta=0.1, use_x0=False):
+                     precision=PREC_F64, tol=1e-10, maxiter=100000, delta=0.0, use_x0=False):
         return SolveParams(self.Ls, alpha, M5, system, mf, m1, m2, shift, precision, tol, maxiter, delta,
                            int(use_x0))
 

@@ -164,3 +164,16 @@ def test_h_shift_identity():
     a = eofa.system_apply(U, psi, 2.0, 1.8, 0.04, 1.0, "R", -1.0, -1)
     b = eofa.system_apply(U, psi, 2.0, 1.8, 0.04, 1.0, "L", -1.0, -1)
     assert np.linalg.norm(a - b) < 1e-13 * np.linalg.norm(a)
+
+
+def test_single_site_hop_matches_whole_field():
+    dims = (4, 2, 2, 4)
+    U = inputs.gauge_field(dims, 0.6, 12)
+    psi = _rand(dims, 3, 9)
+    for bc in (-1, 1):
+        for dag in (False, True):
+            full = dwf.wilson_hop(U, psi, bc, dagger=dag)
+            for site in ((0, 0, 0, 0), (3, 1, 1, 3), (3, 0, 1, 2), (1, 1, 0, 0)):
+                for s in range(3):
+                    got = dwf.wilson_hop_at(U, psi, site, s, bc, dagger=dag)
+                    assert np.abs(got - full[(s,) + site]).max() < 1e-14
