@@ -444,10 +444,12 @@ def main():
 
 
 def kernel_version():
-    """Hash of the hop kernel source, to invalidate stored ncu traffic when it changes."""
+    """Hash of the dslash kernel sources, to invalidate stored ncu traffic when they change."""
     import hashlib
-    src = open(os.path.join(ROOT, "paper_1611_00298_gb300", "csrc", "dslash.cu"), "rb").read()
-    return hashlib.sha256(src).hexdigest()[:16]
+    h = hashlib.sha256()
+    for f in ("dslash_impl.cuh", "field.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1611_00298_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
 
 
 if __name__ == "__main__":

@@ -4,7 +4,7 @@
 // alone leaves most of the GPU idle and is bound by launch latency.
 //
 // Every system keeps its own reduction scratch and device scalars, so the
-// iterations of all active systems can run concurrently: a chunk of 8 CG
+// iterations of all active systems can run concurrently: a chunk of 16 CG
 // iterations of every active system is captured once into a CUDA graph
 // (one stream per system, forked from and joined to an origin stream) and
 // replayed; between replays the host reads each system's residual, does
@@ -15,7 +15,7 @@
 #include <chrono>
 #include <memory>
 
-#define BATCH_CHUNK 8
+#define BATCH_CHUNK 16
 
 extern "C" int eofa_solve_batched(eofa_ctx* const* ctxs, int n, const eofa_solve_params* params,
                                   const double* const* b, double* const* x, eofa_solve_info* info) {
@@ -31,11 +31,13 @@ extern "C" int eofa_solve_batched(eofa_ctx* const* ctxs, int n, const eofa_solve
     cudaGraphExec_t exec = nullptr;
     std::vector<cudaEvent_t> evs;
     std::vector<bool> prof_saved(n, false);
+    double* rr_host = nullptr;
     int rc = EOFA_OK;
     try {
         std::vector<Solve> sv(n);
         std::vector<double*> bdev(n), xdev(n);
         EOFA_CUDA(cudaStreamCreateWithFlags(&origin, cudaStreamNonBlocking));
+        EOFA_CUDA(cudaMallocHost((void**)&rr_host, n * sizeof(double)));
         for (int i = 0; i < n; i++) {
             errctx = ctxs[i];
             EOFA_CUDA(cudaStreamCreateWithFlags(&streams[i], cudaStreamNonBlocking));
@@ -112,10 +114,16 @@ extern "C" int eofa_solve_batched(eofa_ctx* const* ctxs, int n, const eofa_solve
             EOFA_CUDA(cudaGraphLaunch(exec, origin));
             EOFA_CUDA(cudaStreamSynchronize(origin));
             // each system's iteration counter stays a multiple of the chunk, so the
-            // parities and residual-ring slots baked into the graph stay valid
-            for (int i : active) {
+            // parities and residual-ring slots baked into the graph stay valid;
+            // all residuals come back in one round trip
+            for (size_t a = 0; a < active.size(); a++)
+                EOFA_CUDA(cudaMemcpyAsync(rr_host + a, sv[active[a]].last_rr(), sizeof(double),
+                                          cudaMemcpyDeviceToHost, origin));
+            EOFA_CUDA(cudaStreamSynchronize(origin));
+            for (size_t a = 0; a < active.size(); a++) {
+                int i = active[a];
                 errctx = ctxs[i];
-                sv[i].check(BATCH_CHUNK, streams[i]);
+                sv[i].check_value(rr_host[a], streams[i]);
             }
         }
         for (int i = 0; i < n; i++) {
@@ -152,5 +160,6 @@ extern "C" int eofa_solve_batched(eofa_ctx* const* ctxs, int n, const eofa_solve
             cudaStreamDestroy(s);
         }
     if (origin) cudaStreamDestroy(origin);
+    if (rr_host) cudaFreeHost(rr_host);
     return rc;
 }

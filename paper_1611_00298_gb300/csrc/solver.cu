@@ -183,8 +183,9 @@ void Solve::enqueue(int n, cudaStream_t st) {
     inf.iters += n;
 }
 
-void Solve::check(int n, cudaStream_t st) {
-    double rr = fetch_one(ctx, red + SC_RRH + ((it - 1) % ring), st);
+void Solve::check(int n, cudaStream_t st) { check_value(fetch_one(ctx, last_rr(), st), st); }
+
+void Solve::check_value(double rr, cudaStream_t st) {
     if (!is_finite(rr)) throw eofa_error(EOFA_ENUMERIC, "NaN/Inf in CG");
     double rn = std::sqrt(rr);
     if (!mixed) {

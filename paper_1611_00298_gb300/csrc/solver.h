@@ -34,6 +34,10 @@ struct Solve {
     void enqueue(int n, cudaStream_t st);
     // after a queued chunk: read |r|^2, do a reliable update if due; sets done when the inner target is met
     void check(int n, cudaStream_t st);
+    // the same with |r|^2 already read back by the caller
+    void check_value(double rr, cudaStream_t st);
+    // device address of the |r|^2 written by the last queued iteration
+    const double* last_rr() const { return red + SC_RRH + ((it + ring - 1) % ring); }
     // fold the inner solution into x_o, reconstruct, compute the true residual; true when finished
     bool finish(double* x_dev, cudaStream_t st);
 };
