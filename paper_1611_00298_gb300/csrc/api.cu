@@ -6,6 +6,7 @@
 
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 
 // ------------------------------------------------------------------ context helpers
@@ -161,6 +162,12 @@ int eofa_create(eofa_ctx** out, const int dims[4], int Ls, int bc_t, int flags) 
     ctx->stream = nullptr;
     ctx->prof = nullptr;
     ctx->tuned = new std::map<long long, int>();
+    ctx->forced_cfg = 0;
+    if (const char* env = getenv("EOFA_DSLASH_CONFIG")) {
+        int ns = 0, spt = 0;
+        if (sscanf(env, "%d,%d", &ns, &spt) == 2 && ns >= 1 && ns <= 64 && (spt == 1 || spt == 2))
+            ctx->forced_cfg = ns * 4 + spt;
+    }
     ctx->rel_delta = 0.0;  // precision default
     try {
         EOFA_CUDA(cudaGetDevice(&ctx->device));

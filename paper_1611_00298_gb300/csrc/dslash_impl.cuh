@@ -71,56 +71,72 @@ __device__ __forceinline__ void link_row<float>(const void* g, long long idx, in
     }
 }
 
-// acc += (1 + SG gamma_mu) V psi (V = U or U^+), negated when neg.  Few
-// registers stay live: the two half-spinor rows h0, h1 are formed first,
-// then the link is read one row at a time; row a gives component a of
-// W_k = V h_k, which adds to the upper spins and, through A^+, to the lower.
-template <int MU, int SG, bool DAGLINK, typename R>
-__device__ __forceinline__ void hop_dir(const cpx<R>* psi, const void* gauge, long long lidx, bool neg,
-                                        cpx<R>* acc) {
-    cpx<R> a0[3], a1[3], h0[3], h1[3];
+// (1 + SG gamma_mu) psi has upper half h = psi_u + SG A psi_l (two colour
+// vectors h0, h1) and lower half SG A^+ h.  project forms h (negated for a
+// boundary phase of -1); mac_row adds row a of V h (V = U or U^+, one link
+// row u) to the upper spins and, through A^+, to the lower spins.
+template <int MU, int SG, typename R>
+__device__ __forceinline__ void project(const cpx<R>* psi, bool neg, cpx<R>* h) {
+    cpx<R> a0[3], a1[3];
     apply_A<MU>(psi + 6, psi + 9, a0, a1);
 #pragma unroll
     for (int c = 0; c < 3; c++) {
-        h0[c] = SG > 0 ? psi[c] + a0[c] : psi[c] - a0[c];
-        h1[c] = SG > 0 ? psi[3 + c] + a1[c] : psi[3 + c] - a1[c];
+        h[c] = SG > 0 ? psi[c] + a0[c] : psi[c] - a0[c];
+        h[3 + c] = SG > 0 ? psi[3 + c] + a1[c] : psi[3 + c] - a1[c];
         if (neg) {
-            h0[c] = mk(-h0[c].re, -h0[c].im);
-            h1[c] = mk(-h1[c].re, -h1[c].im);
+            h[c] = mk(-h[c].re, -h[c].im);
+            h[3 + c] = mk(-h[3 + c].re, -h[3 + c].im);
         }
-    }
-#pragma unroll
-    for (int a = 0; a < 3; a++) {
-        cpx<R> u[3];
-        link_row<R>(gauge, lidx, a, DAGLINK, u);
-        const cpx<R> w0 = cmul(u[0], h0[0]) + cmul(u[1], h0[1]) + cmul(u[2], h0[2]);
-        const cpx<R> w1 = cmul(u[0], h1[0]) + cmul(u[1], h1[1]) + cmul(u[2], h1[2]);
-        acc[a] = acc[a] + w0;
-        acc[3 + a] = acc[3 + a] + w1;
-        // lower spins: SG (A^+ W)
-        cpx<R> l0, l1;
-        if (MU == 0) { l0 = itimes(w1); l1 = itimes(w0); }
-        else if (MU == 1) { l0 = w1; l1 = mk(-w0.re, -w0.im); }
-        else if (MU == 2) { l0 = itimes(w0); l1 = mitimes(w1); }
-        else { l0 = w0; l1 = w1; }
-        acc[6 + a] = SG > 0 ? acc[6 + a] + l0 : acc[6 + a] - l0;
-        acc[9 + a] = SG > 0 ? acc[9 + a] + l1 : acc[9 + a] - l1;
     }
 }
 
-template <int P, int DAG, int MU>
-__device__ __forceinline__ void hop_mu(const Geom& g, int par, int j, int s, int Ls, long long n5, const void* in,
-                                       const void* gauge, cpx<typename Field<P>::R>* acc) {
+template <int MU, int SG, typename R>
+__device__ __forceinline__ void mac_row(const cpx<R>* u, int a, const cpx<R>* h, cpx<R>* acc) {
+    const cpx<R> w0 = cmul(u[0], h[0]) + cmul(u[1], h[1]) + cmul(u[2], h[2]);
+    const cpx<R> w1 = cmul(u[0], h[3]) + cmul(u[1], h[4]) + cmul(u[2], h[5]);
+    acc[a] = acc[a] + w0;
+    acc[3 + a] = acc[3 + a] + w1;
+    cpx<R> l0, l1;
+    if (MU == 0) { l0 = itimes(w1); l1 = itimes(w0); }
+    else if (MU == 1) { l0 = w1; l1 = mk(-w0.re, -w0.im); }
+    else if (MU == 2) { l0 = itimes(w0); l1 = mitimes(w1); }
+    else { l0 = w0; l1 = w1; }
+    acc[6 + a] = SG > 0 ? acc[6 + a] + l0 : acc[6 + a] - l0;
+    acc[9 + a] = SG > 0 ? acc[9 + a] + l1 : acc[9 + a] - l1;
+}
+
+// One direction pair for SPT slices s[0..SPT) of site j: the neighbour index
+// and every link row are loaded once and used for all SPT slices.
+template <int P, int DAG, int MU, int SPT>
+__device__ __forceinline__ void hop_mu(const Geom& g, int par, int j, const int* sv, int Ls, long long n5,
+                                       const void* in, const void* gauge, cpx<typename Field<P>::R> (*acc)[12]) {
     typedef typename Field<P>::R R;
-    cpx<R> psi[12];
     const int* nb = par ? g.nbr[1] : g.nbr[0];
-    int e = __ldg(nb + (2 * MU) * g.Vh + j);
-    Field<P>::load(in, e & 0x7fffffff, s, Ls, n5, psi);
-    hop_dir<MU, DAG ? 1 : -1, false>(psi, gauge, (long long)((par * 4 + MU) * g.Vh + j), e < 0, acc);
-    e = __ldg(nb + (2 * MU + 1) * g.Vh + j);
-    const int jn = e & 0x7fffffff;
-    Field<P>::load(in, jn, s, Ls, n5, psi);
-    hop_dir<MU, DAG ? -1 : 1, true>(psi, gauge, (long long)(((1 - par) * 4 + MU) * g.Vh + jn), e < 0, acc);
+#pragma unroll
+    for (int dirn = 0; dirn < 2; dirn++) {
+        const int e = __ldg(nb + (2 * MU + dirn) * g.Vh + j);
+        const int jn = e & 0x7fffffff;
+        cpx<R> h[SPT][6];
+#pragma unroll
+        for (int k = 0; k < SPT; k++) {
+            cpx<R> psi[12];
+            Field<P>::load(in, jn, sv[k], Ls, n5, psi);
+            if (dirn == 0) project<MU, DAG ? 1 : -1>(psi, e < 0, h[k]);
+            else project<MU, DAG ? -1 : 1>(psi, e < 0, h[k]);
+        }
+        const long long lidx = dirn == 0 ? (long long)((par * 4 + MU) * g.Vh + j)
+                                         : (long long)(((1 - par) * 4 + MU) * g.Vh + jn);
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            cpx<R> u[3];
+            link_row<R>(gauge, lidx, a, dirn == 1, u);
+#pragma unroll
+            for (int k = 0; k < SPT; k++) {
+                if (dirn == 0) mac_row<MU, DAG ? 1 : -1>(u, a, h[k], acc[k]);
+                else mac_row<MU, DAG ? -1 : 1>(u, a, h[k], acc[k]);
+            }
+        }
+    }
 }
 
 // ---------------------------------------------------------------- 5D-local column ops
@@ -355,8 +371,11 @@ __device__ __forceinline__ double cg_beta(const double* sc, int it) {
 
 // HASOP = false: B is the identity (plain hop), compiled separately so that
 // the register budget of the hop is not set by the 5D-local recurrences.
-template <int P, int DAG, int LS, bool HASOP>
-__global__ void __launch_bounds__(256, HASOP ? EOFA_DSLASH_MINB : EOFA_HOP_MINB) dslash_kernel(
+// SPT slices per thread: thread (site, sh) handles s = sh + k Ls/SPT,
+// k < SPT, so neighbour indices and link rows are loaded once for SPT output
+// sites (Ls/SPT threads per site; SPT = 2 needs an even Ls).
+template <int P, int DAG, int LS, bool HASOP, int SPT>
+__global__ void __launch_bounds__(256, SPT == 2 ? 2 : (HASOP ? EOFA_DSLASH_MINB : EOFA_HOP_MINB)) dslash_kernel(
     Geom g, int par, const void* __restrict__ in, void* out, const void* __restrict__ gauge, Op5 op, const void* y,
     double a_out, double b_in, double* red, int slot, int NS) {
     typedef typename Field<P>::R R;
@@ -364,29 +383,36 @@ __global__ void __launch_bounds__(256, HASOP ? EOFA_DSLASH_MINB : EOFA_HOP_MINB)
     cpx<R>* sm = reinterpret_cast<cpx<R>*>(smraw);
     const int Ls = LS > 0 ? LS : g.Ls;
     const int LsP = Ls + 1;
+    const int Lt = Ls / SPT;  // threads per site
     const long long n5 = (long long)g.Vh * Ls;
-    const int ls = threadIdx.x / Ls, s = threadIdx.x - ls * Ls;
+    const int ls = threadIdx.x / Lt, sh = threadIdx.x - ls * Lt;
+    int sv[SPT];
+#pragma unroll
+    for (int k = 0; k < SPT; k++) sv[k] = sh + k * Lt;
     const bool active_thread = ls < NS;
-    const bool ident = !HASOP;
     const int ntiles = (g.Vh + NS - 1) / NS;
     const R scale = (R)(-0.5 * a_out);
     double nacc = 0.0;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int j = tile * NS + ls;
         const bool site_ok = active_thread && j < g.Vh;
-        cpx<R> acc[12];
+        cpx<R> acc[SPT][12];
 #pragma unroll
-        for (int c = 0; c < 12; c++) acc[c] = mk(R(0), R(0));
+        for (int k = 0; k < SPT; k++)
+#pragma unroll
+            for (int c = 0; c < 12; c++) acc[k][c] = mk(R(0), R(0));
         if (site_ok) {
-            hop_mu<P, DAG, 0>(g, par, j, s, Ls, n5, in, gauge, acc);
-            hop_mu<P, DAG, 1>(g, par, j, s, Ls, n5, in, gauge, acc);
-            hop_mu<P, DAG, 2>(g, par, j, s, Ls, n5, in, gauge, acc);
-            hop_mu<P, DAG, 3>(g, par, j, s, Ls, n5, in, gauge, acc);
+            hop_mu<P, DAG, 0, SPT>(g, par, j, sv, Ls, n5, in, gauge, acc);
+            hop_mu<P, DAG, 1, SPT>(g, par, j, sv, Ls, n5, in, gauge, acc);
+            hop_mu<P, DAG, 2, SPT>(g, par, j, sv, Ls, n5, in, gauge, acc);
+            hop_mu<P, DAG, 3, SPT>(g, par, j, sv, Ls, n5, in, gauge, acc);
         }
-        if (!ident) {
+        if (HASOP) {
             if (site_ok) {
 #pragma unroll
-                for (int c = 0; c < 12; c++) sts(sm + (ls * 12 + c) * LsP + s, acc[c]);
+                for (int k = 0; k < SPT; k++)
+#pragma unroll
+                    for (int c = 0; c < 12; c++) sts(sm + (ls * 12 + c) * LsP + sv[k], acc[k][c]);
             }
             __syncthreads();
             const int nsites = min(NS, g.Vh - tile * NS);
@@ -395,23 +421,28 @@ __global__ void __launch_bounds__(256, HASOP ? EOFA_DSLASH_MINB : EOFA_HOP_MINB)
             __syncthreads();
             if (site_ok) {
 #pragma unroll
-                for (int c = 0; c < 12; c++) acc[c] = lds(sm + (ls * 12 + c) * LsP + s);
+                for (int k = 0; k < SPT; k++)
+#pragma unroll
+                    for (int c = 0; c < 12; c++) acc[k][c] = lds(sm + (ls * 12 + c) * LsP + sv[k]);
             }
         }
         if (site_ok) {
 #pragma unroll
-            for (int c = 0; c < 12; c++) acc[c] = scale * acc[c];
-            if (y != nullptr) {
-                cpx<R> yv[12];
-                Field<P>::load(y, j, s, Ls, n5, yv);
-                const R bb = (R)b_in;
+            for (int k = 0; k < SPT; k++) {
 #pragma unroll
-                for (int c = 0; c < 12; c++) acc[c] = acc[c] + bb * yv[c];
+                for (int c = 0; c < 12; c++) acc[k][c] = scale * acc[k][c];
+                if (y != nullptr) {
+                    cpx<R> yv[12];
+                    Field<P>::load(y, j, sv[k], Ls, n5, yv);
+                    const R bb = (R)b_in;
+#pragma unroll
+                    for (int c = 0; c < 12; c++) acc[k][c] = acc[k][c] + bb * yv[c];
+                }
+                Field<P>::store(out, j, sv[k], Ls, n5, acc[k]);
+                if (red) nacc += site_norm2<R>(acc[k]);
             }
-            Field<P>::store(out, j, s, Ls, n5, acc);
-            if (red) nacc += site_norm2<R>(acc);
         }
-        if (!ident) __syncthreads();
+        if (HASOP) __syncthreads();
     }
     if (red) grid_sum(nacc, red, slot);
 }
@@ -536,10 +567,10 @@ unsigned grid_size(K kernel, int threads, size_t smem, int ntiles, int sms) {
 // launches are harmless.  Small lattices, and launches during stream capture,
 // use the heuristic.
 template <typename K>
-void launch_with(K k, const eofa_ctx* ctx, const Geom& g, int NS, size_t elem, bool hasop, int par, const void* in,
-                 void* out, const void* gauge, const Op5& op, const void* y, double a_out, double b_in, double* red,
-                 int slot, cudaStream_t st) {
-    const int threads = (NS * g.Ls + 31) / 32 * 32;
+void launch_with(K k, const eofa_ctx* ctx, const Geom& g, int NS, int spt, size_t elem, bool hasop, int par,
+                 const void* in, void* out, const void* gauge, const Op5& op, const void* y, double a_out, double b_in,
+                 double* red, int slot, cudaStream_t st) {
+    const int threads = (NS * (g.Ls / spt) + 31) / 32 * 32;
     const size_t smem = hasop ? (size_t)NS * 12 * (g.Ls + 1) * elem : 0;
     const int ntiles = (g.Vh + NS - 1) / NS;
     if (smem > 40 * 1024) EOFA_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -547,34 +578,49 @@ void launch_with(K k, const eofa_ctx* ctx, const Geom& g, int NS, size_t elem, b
     k<<<grid, threads, smem, st>>>(g, par, in, out, gauge, op, y, a_out, b_in, red, slot, NS);
 }
 
-template <typename K>
-int tuned_ns(K k, const eofa_ctx* ctx, const Geom& g, long long key, int ns0, size_t elem, bool hasop, int par,
-             const void* in, void* out, const void* gauge, const Op5& op, const void* y, double a_out, double b_in,
-             double* red, int slot, cudaStream_t st) {
+// Autotuned configuration: sites per tile NS and slices per thread SPT,
+// encoded as NS * 4 + SPT.
+template <typename K1, typename K2>
+int tuned_cfg(K1 k1, K2 k2, bool spt2_ok, const eofa_ctx* ctx, const Geom& g, long long key, int ns0, size_t elem,
+              bool hasop, int par, const void* in, void* out, const void* gauge, const Op5& op, const void* y,
+              double a_out, double b_in, double* red, int slot, cudaStream_t st) {
+    if (ctx->forced_cfg) {
+        const int ns = ctx->forced_cfg / 4, spt = ctx->forced_cfg % 4;
+        if ((ns * (g.Ls / spt) + 31) / 32 * 32 <= 256 && (!hasop || (size_t)ns * 12 * (g.Ls + 1) * elem <= 64 * 1024))
+            return (spt == 2 && !spt2_ok) ? ns * 4 + 1 : ctx->forced_cfg;
+    }
     auto it = ctx->tuned->find(key);
     if (it != ctx->tuned->end()) return it->second;
+    const int def = ns0 * 4 + 1;
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     EOFA_CUDA(cudaStreamIsCapturing(st, &cs));
-    if (cs != cudaStreamCaptureStatusNone || (long long)g.Vh * g.Ls < (1LL << 20)) return ns0;
-    int cand[3] = {ns0 / 2, ns0, ns0 * 2};
-    int best = ns0;
+    if (cs != cudaStreamCaptureStatusNone || (long long)g.Vh * g.Ls < (1LL << 20)) return def;
+    int best = def;
     float best_ms = 1e30f;
     cudaEvent_t e0, e1;
     EOFA_CUDA(cudaEventCreate(&e0));
     EOFA_CUDA(cudaEventCreate(&e1));
-    for (int c : cand) {
-        if (c < 1 || c * g.Ls > 512 || (hasop && (size_t)c * 12 * (g.Ls + 1) * elem > 64 * 1024)) continue;
-        launch_with(k, ctx, g, c, elem, hasop, par, in, out, gauge, op, y, a_out, b_in, red, slot, st);  // warm
-        EOFA_CUDA(cudaEventRecord(e0, st));
-        for (int r = 0; r < 3; r++)
-            launch_with(k, ctx, g, c, elem, hasop, par, in, out, gauge, op, y, a_out, b_in, red, slot, st);
-        EOFA_CUDA(cudaEventRecord(e1, st));
-        EOFA_CUDA(cudaEventSynchronize(e1));
-        float ms = 0.f;
-        EOFA_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-        if (ms < best_ms) {
-            best_ms = ms;
-            best = c;
+    for (int spt = 1; spt <= 2; spt++) {
+        if (spt == 2 && !spt2_ok) continue;
+        for (int c : {ns0 / 2, ns0, ns0 * 2, ns0 * 4}) {
+            if (c < 1 || (c * (g.Ls / spt) + 31) / 32 * 32 > 256 ||
+                (hasop && (size_t)c * 12 * (g.Ls + 1) * elem > 64 * 1024))
+                continue;
+            auto run = [&]() {
+                if (spt == 1) launch_with(k1, ctx, g, c, 1, elem, hasop, par, in, out, gauge, op, y, a_out, b_in, red, slot, st);
+                else launch_with(k2, ctx, g, c, 2, elem, hasop, par, in, out, gauge, op, y, a_out, b_in, red, slot, st);
+            };
+            run();  // warm
+            EOFA_CUDA(cudaEventRecord(e0, st));
+            for (int r = 0; r < 3; r++) run();
+            EOFA_CUDA(cudaEventRecord(e1, st));
+            EOFA_CUDA(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            EOFA_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = c * 4 + spt;
+            }
         }
     }
     EOFA_CUDA(cudaEventDestroy(e0));
@@ -591,11 +637,18 @@ void launch_dslash_t(const eofa_ctx* ctx, int par, const void* in, void* out, co
     Geom g = ctx_geom(ctx);
     const void* gauge = ctx->gauge[P == P64 ? P64 : P32];
     const bool hasop = op.inv[0] || op.inv[1] || op.fwd[0] || op.fwd[1] || op.sigma[0] != 0.0 || op.sigma[1] != 0.0;
-    auto k = hasop ? dslash_kernel<P, DAG, LS, true> : dslash_kernel<P, DAG, LS, false>;
+    // two slices per thread (SPT = 2) was measured slower than one in every
+    // tile shape at 24^3 x 64 x 24 (0.79 vs 0.69 ms, FP32 hop); only SPT = 1 is built
+    constexpr bool SPT2 = false;
+    constexpr int S2 = SPT2 ? 2 : 1;
+    auto k1 = hasop ? dslash_kernel<P, DAG, LS, true, 1> : dslash_kernel<P, DAG, LS, false, 1>;
+    auto k2 = hasop ? dslash_kernel<P, DAG, LS, true, S2> : dslash_kernel<P, DAG, LS, false, S2>;
     const long long key = ((((long long)P * 2 + DAG) * 128 + g.Ls) * 2 + (hasop ? 1 : 0)) * 2 + (y ? 1 : 0);
-    const int NS = tuned_ns(k, ctx, g, key, pick_ns(g.Ls, sizeof(cpx<R>)), sizeof(cpx<R>), hasop, par, in, out, gauge,
-                            op, y, a_out, b_in, red, slot, st);
-    launch_with(k, ctx, g, NS, sizeof(cpx<R>), hasop, par, in, out, gauge, op, y, a_out, b_in, red, slot, st);
+    const int cfg = tuned_cfg(k1, k2, SPT2, ctx, g, key, pick_ns(g.Ls, sizeof(cpx<R>)), sizeof(cpx<R>), hasop, par, in,
+                              out, gauge, op, y, a_out, b_in, red, slot, st);
+    const int NS = cfg / 4, spt = cfg % 4;
+    if (spt == 2) launch_with(k2, ctx, g, NS, 2, sizeof(cpx<R>), hasop, par, in, out, gauge, op, y, a_out, b_in, red, slot, st);
+    else launch_with(k1, ctx, g, NS, 1, sizeof(cpx<R>), hasop, par, in, out, gauge, op, y, a_out, b_in, red, slot, st);
     EOFA_LAUNCHED();
 }
 

@@ -122,7 +122,8 @@ struct eofa_ctx {
     std::map<std::string, void*> bufs;  // named workspace fields
     std::map<std::string, size_t> buf_sizes;
     Prof* prof;
-    std::map<long long, int>* tuned;  // autotuned sites-per-tile of the fused dslash, by kernel key
+    std::map<long long, int>* tuned;  // autotuned dslash configuration (NS * 4 + SPT), by kernel key
+    int forced_cfg;                   // EOFA_DSLASH_CONFIG="NS,SPT" at context creation (0: autotune)
     double rel_delta;  // reliable-update threshold of the solves inside action / force / MD
 };
 

@@ -171,3 +171,41 @@ def test_schur_hop_parity(eofa, case, prec, tol):
             torch.cuda.synchronize()
             got = res.cpu().numpy()
             assert _rel(got, ref) < tol, (out_par, dag, _rel(got, ref))
+
+
+@pytest.mark.parametrize("cfg", ["2,1", "4,1", "8,1"])
+def test_forced_dslash_configurations(eofa, cfg, monkeypatch):
+    """Every tile shape / slices-per-thread variant the autotuner may pick gives the same fused kernel result."""
+    import torch
+    monkeypatch.setenv("EOFA_DSLASH_CONFIG", cfg)
+    dims, Ls, alpha, M5, mf, bc = (4, 4, 2, 4), 24, 2.0, 1.8, 0.0362, -1
+    lat, U = _setup(eofa, dims, Ls, bc)
+    psi = inputs.fermion5d(dims, Ls, 7)
+    X, Y, Z, T = dims
+    t, z, y, x = np.meshgrid(*[np.arange(n) for n in (T, Z, Y, X)], indexing="ij")
+    par = (x + y + z + t) % 2
+    Gp, Gm = _ginv_blocks(Ls, alpha, M5, mf)
+    for prec, tol in ((1, 2e-6), (2, 3e-3)):
+        nb = lat.field_bytes(prec)
+        for schur in (False, True):
+            src = psi * (par == 1)[None, :, :, :, :, None, None]
+            ref = dwf.wilson_hop(U, src, bc)
+            if schur:
+                ref = dwf.apply_s(Gp, Gm, ref)
+            ref = ref * (par == 0)[None, :, :, :, :, None, None]
+            dev = torch.from_numpy(src.copy()).cuda()
+            ev = torch.empty(nb, dtype=torch.uint8, device="cuda")
+            od = torch.empty_like(ev)
+            out = torch.empty_like(ev)
+            zero = torch.zeros_like(ev)
+            lat.pack_dev(prec, dev, ev, od)
+            lat.pack_dev(prec, torch.zeros_like(dev), zero, zero)
+            if schur:
+                lat.schur_hop_dev(prec, 0, 0, od, out, alpha, M5, mf)
+            else:
+                lat.hop_dev(prec, 0, 0, od, out)
+            res = torch.empty_like(dev)
+            lat.unpack_dev(prec, out, zero, res)
+            torch.cuda.synchronize()
+            assert _rel(res.cpu().numpy(), ref) < tol, (cfg, prec, schur)
+    lat.close()
