@@ -202,6 +202,24 @@ int eofa_leapfrog_dev(eofa_ctx* ctx, int Ls, double alpha, double M5, double m1,
                       double tol, int nsteps, double dtau, const double* phi_dev, double* P_dev, double* U_dev,
                       double* dH, double* H0, void* stream);
 
+/* Rational approximation for the heatbath (Sec. 3.2):
+ * x^{-1/2} ~ alpha0 + sum_{l<npoles} alpha[l] / (x + beta[l]) on [lmin, lmax]
+ * (0 < lmin < lmax), Zolotarev's optimal relative approximation; max_rel_err
+ * (may be NULL) gets its maximum relative error.  alpha, beta: host arrays of
+ * npoles (1..64) doubles.  Host-only: needs no GPU. */
+int eofa_rational_inv_sqrt(int npoles, double lmin, double lmax, double* alpha0, double* alpha, double* beta,
+                           double* max_rel_err);
+
+/* EOFA heatbath, Eq. (6): phi = f(M_EOFA) eta with f(x) = alpha0 + sum_l
+ * alphas[l] / (x + betas[l]) (betas > 0), from 2 npoles solves of Eq. (8).
+ * eta, phi: 4D canonical device fields.  forecast = 1 starts each solve from
+ * the minimal-residual combination of up to 6 earlier solutions of the same
+ * family (chronological inversion, Sec. 5.2); 0 starts from zero.  info (may
+ * be NULL) gets 2 npoles records: pole l, P_- system at 2l, P_+ at 2l + 1. */
+int eofa_heatbath_dev(eofa_ctx* ctx, int Ls, double alpha, double M5, double m1, double m2, int precision,
+                      double tol, int npoles, double alpha0, const double* alphas, const double* betas,
+                      const double* eta_dev, double* phi_dev, int forecast, eofa_solve_info* info, void* stream);
+
 /* Molecular dynamics link update U <- exp(i eps P) U on the device gauge
  * field of the context and on the canonical copy U_dev (if not NULL);
  * P: 4 V traceless Hermitian 3x3, canonical, device. */

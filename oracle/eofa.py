@@ -239,3 +239,24 @@ def force_at_link(U, chiL, chiR, k, bc_t, site, mu):
                 val += -0.5 * (np.vdot(zeta_x, t1) + np.vdot(zeta_f, t2))
             F += sign * k * val.real * T[a]
     return F
+
+
+# ---------------------------------------------------------------- heatbath (Sec. 3.2)
+
+def heatbath(U, eta, Ls, alpha, M5, m1, m2, bc_t, alpha0, alphas, betas, tol=1e-12):
+    """phi = f(M_EOFA) eta for f(x) = alpha0 + sum_l alphas[l] / (x + betas[l]), Eq. (6).
+
+    With gamma_l = 1 / (1 + beta_l), each pole needs one solve of Eq. (8) for
+    the P_- part (H(m1) - gamma_l Delta_- P_-) and one for the P_+ part
+    (H(m2) - gamma_l beta_l Delta_+ P_+).
+    """
+    Op, Om = omega(Ls, alpha)
+    k = k_coefficient(Ls, alpha, m1, m2)
+    bL, bR = embed(eta, Om, -1), embed(eta, Op, +1)
+    phi = alpha0 * eta
+    for al, be in zip(alphas, betas):
+        g = 1.0 / (1.0 + be)
+        psiL, _, _ = system_solve(U, bL, alpha, M5, m1, m2, "L", -g, bc_t, tol)
+        psiR, _, _ = system_solve(U, bR, alpha, M5, m1, m2, "R", -g * be, bc_t, tol)
+        phi = phi + al * g * (eta + k * g * contract(psiL, Om, -1) - k * g * contract(psiR, Op, +1))
+    return phi

@@ -14,3 +14,6 @@ void apply_eofa_fields(eofa_ctx* ctx, const Op5& G, const void* in_e, const void
 // one solve on device canonical buffers (solver.cu)
 int solve_dev_impl(eofa_ctx* ctx, const eofa_solve_params* p, const double* b_dev, double* x_dev,
                    eofa_solve_info* info, cudaStream_t st);
+
+// Omega_chi P_chi phi: 4D canonical phi -> 5D canonical out (Omega on the device, Ls values)
+void eofa_embed(eofa_ctx* ctx, const double* phi, const double* Om_dev, int chi, double* out, cudaStream_t st);

@@ -241,6 +241,12 @@ ChiBufs eofa_chis(eofa_ctx* ctx, int Ls, double alpha, double M5, double m1, dou
 
 }  // namespace
 
+void eofa_embed(eofa_ctx* ctx, const double* phi, const double* Om_dev, int chi, double* out, cudaStream_t st) {
+    long long V = ctx->V, n = V * 12 * ctx->Ls;
+    embed_kernel<<<nblk(n, 256), 256, 0, st>>>(V, ctx->Ls, (const double2*)phi, Om_dev, chi, (double2*)out);
+    EOFA_LAUNCHED();
+}
+
 int eofa_chis_to(eofa_ctx* ctx, int Ls, double alpha, double M5, double m1, double m2, int precision, double tol,
                  const double* phi_dev, double* chiL, double* chiR, double* S, eofa_solve_info info[2], cudaStream_t st) {
     int rc = EOFA_OK;

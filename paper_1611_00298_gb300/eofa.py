@@ -31,7 +31,7 @@ EXPORTS = [
     "eofa_force_from_chi_dev", "eofa_grad_from_chi_dev", "eofa_coefficients", "eofa_link_update_dev",
     "eofa_solve_batched", "eofa_kernel_launches", "eofa_profile_start", "eofa_profile_stop",
     "eofa_dwf_apply_noalloc", "eofa_schur_hop_dev", "eofa_pseudofermion_solutions_dev",
-    "eofa_set_reliable_delta", "eofa_leapfrog_dev",
+    "eofa_set_reliable_delta", "eofa_leapfrog_dev", "eofa_rational_inv_sqrt", "eofa_heatbath_dev",
 ]
 
 
@@ -105,6 +105,8 @@ def load_library(path: str = LIB_PATH):
         "eofa_pseudofermion_solutions_dev": (I, [P, I, D, D, D, D, I, D, P, P, P, ctypes.POINTER(D),
                                                  ctypes.POINTER(SolveInfo), P]),
         "eofa_set_reliable_delta": (I, [P, D]),
+        "eofa_rational_inv_sqrt": (I, [I, D, D, ctypes.POINTER(D), P, P, ctypes.POINTER(D)]),
+        "eofa_heatbath_dev": (I, [P, I, D, D, D, D, I, D, I, D, P, P, P, P, I, ctypes.POINTER(SolveInfo), P]),
         "eofa_leapfrog_dev": (I, [P, I, D, D, D, D, I, D, I, D, P, P, P, ctypes.POINTER(D), ctypes.POINTER(D), P]),
         "eofa_profile_start": (I, [P]),
         "eofa_profile_stop": (I, [P, ctypes.POINTER(Profile)]),
@@ -134,6 +136,20 @@ def _stream():
 def kernel_launches() -> int:
     """Number of CUDA kernels libeofa has launched since it was loaded."""
     return int(load_library().eofa_kernel_launches())
+
+
+def rational_inv_sqrt(npoles, lmin, lmax):
+    """(alpha0, alpha[], beta[], max relative error) of x^-1/2 ~ alpha0 + sum alpha/(x + beta) on [lmin, lmax]."""
+    lib = load_library()
+    a0 = ctypes.c_double()
+    err = ctypes.c_double()
+    al = np.zeros(npoles)
+    be = np.zeros(npoles)
+    rc = lib.eofa_rational_inv_sqrt(npoles, lmin, lmax, ctypes.byref(a0), al.ctypes.data, be.ctypes.data,
+                                    ctypes.byref(err))
+    if rc != OK:
+        raise EOFAError(rc, "eofa_rational_inv_sqrt")
+    return a0.value, al, be, err.value
 
 
 def coefficients(Ls, alpha, m1, m2):
@@ -336,6 +352,18 @@ class Lattice:
                                                        _ptr(chiL), _ptr(chiR), ctypes.byref(S), info, _stream())
         self._check(rc, "pseudofermion_solutions_dev")
         return S.value, info
+
+    def heatbath_dev(self, eta, phi, alpha, M5, m1, m2, alpha0, alphas, betas, precision=PREC_F64, tol=1e-10,
+                     forecast=True):
+        """phi = f(M_EOFA) eta (Eq. (6)); returns the 2 npoles solve records."""
+        al = np.ascontiguousarray(alphas, dtype=np.float64)
+        be = np.ascontiguousarray(betas, dtype=np.float64)
+        info = (SolveInfo * (2 * len(al)))()
+        rc = self.lib.eofa_heatbath_dev(self.ctx, self.Ls, alpha, M5, m1, m2, precision, tol, len(al), alpha0,
+                                        al.ctypes.data, be.ctypes.data, _ptr(eta), _ptr(phi), int(forecast), info,
+                                        _stream())
+        self._check(rc, "heatbath_dev")
+        return list(info)
 
     def set_reliable_delta(self, delta):
         self._check(self.lib.eofa_set_reliable_delta(self.ctx, delta), "set_reliable_delta")

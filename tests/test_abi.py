@@ -67,3 +67,35 @@ def test_create_without_gpu_reports_error(libpath):
     from paper_1611_00298_gb300 import eofa
     with pytest.raises(eofa.EOFAError):
         eofa.Lattice((4, 4, 4, 4), 8)
+
+
+@pytest.mark.parametrize("n,lmin,lmax", [(4, 0.1, 2.0), (8, 1e-3, 10.0), (12, 1e-4, 50.0)])
+def test_rational_inv_sqrt_is_minimax(libpath, n, lmin, lmax):
+    """Host-only Zolotarev coefficients (Sec. 3.2): the relative error of
+    alpha0 + sum alpha/(x + beta) against x^-1/2 stays within the reported
+    bound and equioscillates at 2n + 2 extrema (Chebyshev's alternation
+    theorem for the optimal (n, n) approximant)."""
+    import numpy as np
+    from paper_1611_00298_gb300 import eofa
+    eofa.load_library(libpath)
+    a0, al, be, err = eofa.rational_inv_sqrt(n, lmin, lmax)
+    assert np.all(be > 0) and np.all(al > 0) and a0 > 0
+    x = np.exp(np.linspace(np.log(lmin), np.log(lmax), 200001))
+    f = a0 + (al[None, :] / (x[:, None] + be[None, :])).sum(1)
+    e = f * np.sqrt(x) - 1.0
+    assert np.abs(e).max() < err * (1 + 1e-6) + 1e-14
+    assert np.abs(e).max() > err * (1 - 1e-3)
+    # sign alternations between successive near-extremal points
+    ext = np.flatnonzero(np.abs(e) > 0.999 * err)
+    groups = np.split(ext, np.flatnonzero(np.diff(ext) > 1) + 1)
+    signs = [np.sign(e[g[np.argmax(np.abs(e[g]))]]) for g in groups]
+    assert len(signs) == 2 * n + 2
+    assert all(signs[i] != signs[i + 1] for i in range(len(signs) - 1))
+
+
+def test_rational_inv_sqrt_error_shrinks_with_poles(libpath):
+    from paper_1611_00298_gb300 import eofa
+    eofa.load_library(libpath)
+    errs = [eofa.rational_inv_sqrt(n, 1e-3, 10.0)[3] for n in (2, 4, 8, 16)]
+    assert all(errs[i + 1] < 0.1 * errs[i] for i in range(3))
+    assert eofa.rational_inv_sqrt(16, 1e-3, 10.0)[3] < 1e-10

@@ -6,6 +6,7 @@ import numpy as np
 import pytest
 
 from oracle import dwf, eofa, solve
+from oracle import eofa as oeofa
 from paper_1611_00298_gb300 import inputs
 from tests._dense import dense
 
@@ -176,3 +177,22 @@ def test_leapfrog_dH_scales_as_dtau_squared_and_reversible(U):
     U2, P2, dHb = eofa.leapfrog(U1, -P1, phi, *args, nsteps=3, dtau=0.1, tol=1e-14)
     assert np.abs(U2 - U).max() < 1e-10
     assert np.abs(P2 + P).max() < 1e-10
+
+
+def test_heatbath_eq6_equals_dense_rational_function(U):
+    """Eq. (6) with arbitrary positive poles equals f(M_EOFA) eta by eigendecomposition."""
+    ML, MR, _, _ = _eofa_matrices(U, ALPHA, M1, M2)
+    M = np.zeros((192, 192), dtype=np.complex128)
+    idx = np.arange(192).reshape(16, 4, 3)
+    sm = idx[:, [2, 3], :].reshape(-1)
+    sp = idx[:, [0, 1], :].reshape(-1)
+    M[np.ix_(sm, sm)] = ML[np.ix_(sm, sm)]
+    M[np.ix_(sp, sp)] = MR[np.ix_(sp, sp)]
+    lam, vec = np.linalg.eigh(M)
+    assert lam.min() > 0
+    eta = inputs.fermion4d(DIMS, 9)
+    a0, al, be = 0.3, np.array([0.7, 0.2, 1.3]), np.array([0.05, 0.9, 4.0])
+    f = a0 + (al[None, :] / (lam[:, None] + be[None, :])).sum(1)
+    exact = (vec @ (f * (vec.conj().T @ eta.reshape(-1)))).reshape(eta.shape)
+    phi = oeofa.heatbath(U, eta, LS, ALPHA, M5, M1, M2, BC, a0, al, be, tol=1e-13)
+    assert np.linalg.norm(phi - exact) < 1e-10 * np.linalg.norm(exact)
