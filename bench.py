@@ -175,13 +175,18 @@ def hop_only(args, wl):
     out = torch.empty_like(e)
     lat.pack_dev(prec, canon, e, o)
     del canon
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record()
-    for _ in range(args.hop_reps):
+
+    def one():
         if args.schur:
             lat.schur_hop_dev(prec, 0, 0, o, out, wl["alpha"], wl["M5"], wl["m1"])
         else:
             lat.hop_dev(prec, 0, 0, o, out)
+    one()  # the first launch runs the tile autotuner
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for _ in range(args.hop_reps):
+        one()
     ev1.record()
     torch.cuda.synchronize()
     ms = ev0.elapsed_time(ev1) / args.hop_reps
@@ -447,7 +452,7 @@ def kernel_version():
     """Hash of the dslash kernel sources, to invalidate stored ncu traffic when they change."""
     import hashlib
     h = hashlib.sha256()
-    for f in ("dslash_impl.cuh", "field.cuh"):
+    for f in ("dslash_impl.cuh", "dslash_bulk.cuh", "field.cuh"):
         h.update(open(os.path.join(ROOT, "paper_1611_00298_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 

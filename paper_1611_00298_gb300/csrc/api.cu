@@ -164,9 +164,12 @@ int eofa_create(eofa_ctx** out, const int dims[4], int Ls, int bc_t, int flags) 
     ctx->tuned = new std::map<long long, int>();
     ctx->forced_cfg = 0;
     if (const char* env = getenv("EOFA_DSLASH_CONFIG")) {
-        int ns = 0, spt = 0;
-        if (sscanf(env, "%d,%d", &ns, &spt) == 2 && ns >= 1 && ns <= 64 && (spt == 1 || spt == 2))
-            ctx->forced_cfg = ns * 4 + spt;
+        // "NS,SPT" selects the direct kernel, "NS,SPT,D" the staged one with ring depth D
+        int ns = 0, spt = 0, depth = 0;
+        const int n = sscanf(env, "%d,%d,%d", &ns, &spt, &depth);
+        if (n >= 2 && ns >= 1 && ns <= 64 && (spt == 1 || spt == 2))
+            ctx->forced_cfg = (n == 3 && depth >= 2 && depth <= 8 && ns <= 32) ? ((1 << 20) | depth << 8 | ns)
+                                                                                : ns * 4 + spt;
     }
     ctx->rel_delta = 0.0;  // precision default
     try {

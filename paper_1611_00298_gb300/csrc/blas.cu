@@ -180,6 +180,18 @@ void red_fetch_many(const eofa_ctx* ctx, int first, int n, double* out, cudaStre
     for (int k = 0; k < n; k++) out[k] = ctx->red_host[k];
 }
 
+void check_device_error(const eofa_ctx* ctx, cudaStream_t st) {
+    int* w = reinterpret_cast<int*>(ctx->red + RED_ERRWORD);
+    int v = 0;
+    EOFA_CUDA(cudaMemcpyAsync(ctx->red_host, w, sizeof(int), cudaMemcpyDeviceToHost, st));
+    EOFA_CUDA(cudaStreamSynchronize(st));
+    v = *reinterpret_cast<int*>(ctx->red_host);
+    if (v != 0) {
+        EOFA_CUDA(cudaMemsetAsync(w, 0, sizeof(int), st));
+        throw eofa_error(EOFA_ETIMEOUT, "a device wait ran out of time (staged dslash)");
+    }
+}
+
 size_t red_scratch_bytes() { return (size_t)RED_TOTAL_DOUBLES * sizeof(double); }
 static_assert(RED_TICKET_OFF + 8 <= RED_PART, "reduction scratch regions overlap");
 

@@ -21,6 +21,9 @@
 #include "field.cuh"
 #include "fused.h"
 
+#include <cstdio>
+#include <cstdlib>
+
 // minimum resident blocks of 256 threads per SM requested from the register
 // allocator (3 -> at most 85 registers, 8 blocks of 96 threads per SM)
 #ifndef EOFA_DSLASH_MINB
@@ -538,6 +541,14 @@ __global__ void __launch_bounds__(256) xp_update_kernel(Geom g, const double* sc
 
 // sites per tile: NS * Ls a multiple of 32 where possible, 96..256 threads,
 // at most 32 KB of shared memory
+}  // namespace
+}  // namespace dsl
+
+#include "dslash_bulk.cuh"
+
+namespace dsl {
+namespace {
+
 inline int pick_ns(int Ls, size_t elem) {
     int gg = 1;
     for (int k = 32; k >= 1; k >>= 1)
@@ -578,16 +589,62 @@ void launch_with(K k, const eofa_ctx* ctx, const Geom& g, int NS, int spt, size_
     k<<<grid, threads, smem, st>>>(g, par, in, out, gauge, op, y, a_out, b_in, red, slot, NS);
 }
 
-// Autotuned configuration: sites per tile NS and slices per thread SPT,
-// encoded as NS * 4 + SPT.
-template <typename K1, typename K2>
-int tuned_cfg(K1 k1, K2 k2, bool spt2_ok, const eofa_ctx* ctx, const Geom& g, long long key, int ns0, size_t elem,
-              bool hasop, int par, const void* in, void* out, const void* gauge, const Op5& op, const void* y,
-              double a_out, double b_in, double* red, int slot, cudaStream_t st) {
+// Staged (bulk-copy) configurations are encoded as CFG_BULK | D << 8 | NS;
+// direct ones as NS * 4 + SPT.
+#define CFG_BULK (1 << 20)
+
+// the EOFA_DSLASH_CONFIG spelling of a configuration
+inline std::string cfg_str(int cfg) {
+    if (cfg & CFG_BULK) return std::to_string(cfg & 0xff) + ",1," + std::to_string((cfg >> 8) & 0xf);
+    return std::to_string(cfg / 4) + "," + std::to_string(cfg % 4);
+}
+
+template <int P>
+bool bulk_fits(const Geom& g, int NS, int D, bool hasop, const void* in, const void* y) {
+    typedef typename Field<P>::R R;
+    if (NS < 1 || NS > 32 || D < 2 || D > 8) return false;
+    if ((NS * g.Ls + 31) / 32 * 32 + 32 > BULK_MAX_THREADS) return false;
+    if (P == P16 && g.Ls % 4 != 0) return false;  // scale rows must be 16-byte multiples
+    if (((uintptr_t)in & 15) || (y && ((uintptr_t)y & 15))) return false;
+    return bulk_plan<P, R>(NS, D, g.Ls, hasop).total_b <= 200 * 1024;
+}
+
+template <int P, typename K>
+void launch_bulk(K k, const eofa_ctx* ctx, const Geom& g, int NS, int D, bool hasop, int par, const void* in,
+                 void* out, const void* gauge, const Op5& op, const void* y, double a_out, double b_in, double* red,
+                 int slot, cudaStream_t st) {
+    typedef typename Field<P>::R R;
+    const BulkPlan pl = bulk_plan<P, R>(NS, D, g.Ls, hasop);
+    const int threads = (NS * g.Ls + 31) / 32 * 32 + 32;
+    const int ntiles = (g.Vh + NS - 1) / NS;
+    if (pl.total_b > 40 * 1024)
+        EOFA_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, pl.total_b));
+    unsigned grid = grid_size(k, threads, pl.total_b, ntiles, ctx->sms);
+    int* err = reinterpret_cast<int*>(ctx->red + RED_ERRWORD);
+    k<<<grid, threads, pl.total_b, st>>>(g, par, in, out, gauge, op, y, a_out, b_in, red, slot, NS, D, err);
+}
+
+// Autotuned configuration, timed once per context and kernel variant with
+// CUDA events on the launching stream: the direct kernel at the heuristic
+// sites per tile NS and its halving / doubling, and the staged kernel at
+// the same NS with ring depths 2 to 4.  The kernels are idempotent (they
+// only write out and the reduction scratch), so the trial launches are
+// harmless.  Small lattices, and launches during stream capture, use the
+// heuristic direct configuration.
+template <int P, typename K1, typename KB>
+int tuned_cfg(K1 k1, KB kb, const eofa_ctx* ctx, const Geom& g, long long key, int ns0, size_t elem, bool hasop,
+              int par, const void* in, void* out, const void* gauge, const Op5& op, const void* y, double a_out,
+              double b_in, double* red, int slot, cudaStream_t st) {
+    auto direct_ok = [&](int c) {
+        return c >= 1 && (c * g.Ls + 31) / 32 * 32 <= 256 && (!hasop || (size_t)c * 12 * (g.Ls + 1) * elem <= 64 * 1024);
+    };
     if (ctx->forced_cfg) {
-        const int ns = ctx->forced_cfg / 4, spt = ctx->forced_cfg % 4;
-        if ((ns * (g.Ls / spt) + 31) / 32 * 32 <= 256 && (!hasop || (size_t)ns * 12 * (g.Ls + 1) * elem <= 64 * 1024))
-            return (spt == 2 && !spt2_ok) ? ns * 4 + 1 : ctx->forced_cfg;
+        const int f = ctx->forced_cfg;
+        if (f & CFG_BULK) {
+            if (bulk_fits<P>(g, f & 0xff, (f >> 8) & 0xf, hasop, in, y)) return f;
+        } else if (direct_ok(f / 4)) {
+            return (f / 4) * 4 + 1;
+        }
     }
     auto it = ctx->tuned->find(key);
     if (it != ctx->tuned->end()) return it->second;
@@ -595,41 +652,49 @@ int tuned_cfg(K1 k1, K2 k2, bool spt2_ok, const eofa_ctx* ctx, const Geom& g, lo
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     EOFA_CUDA(cudaStreamIsCapturing(st, &cs));
     if (cs != cudaStreamCaptureStatusNone || (long long)g.Vh * g.Ls < (1LL << 20)) return def;
+    std::vector<int> cands;
+    for (int c : {ns0 / 2, ns0, ns0 * 2, ns0 * 4})
+        if (direct_ok(c)) cands.push_back(c * 4 + 1);
+    for (int c : {ns0 / 2, ns0, ns0 * 2, ns0 * 4})
+        for (int d = 2; d <= 4; d++)
+            if (bulk_fits<P>(g, c, d, hasop, in, y)) cands.push_back(CFG_BULK | d << 8 | c);
     int best = def;
     float best_ms = 1e30f;
     cudaEvent_t e0, e1;
     EOFA_CUDA(cudaEventCreate(&e0));
     EOFA_CUDA(cudaEventCreate(&e1));
-    for (int spt = 1; spt <= 2; spt++) {
-        if (spt == 2 && !spt2_ok) continue;
-        for (int c : {ns0 / 2, ns0, ns0 * 2, ns0 * 4}) {
-            if (c < 1 || (c * (g.Ls / spt) + 31) / 32 * 32 > 256 ||
-                (hasop && (size_t)c * 12 * (g.Ls + 1) * elem > 64 * 1024))
-                continue;
-            auto run = [&]() {
-                if (spt == 1) launch_with(k1, ctx, g, c, 1, elem, hasop, par, in, out, gauge, op, y, a_out, b_in, red, slot, st);
-                else launch_with(k2, ctx, g, c, 2, elem, hasop, par, in, out, gauge, op, y, a_out, b_in, red, slot, st);
-            };
-            run();  // warm
-            EOFA_CUDA(cudaEventRecord(e0, st));
-            for (int r = 0; r < 3; r++) run();
-            EOFA_CUDA(cudaEventRecord(e1, st));
-            EOFA_CUDA(cudaEventSynchronize(e1));
-            float ms = 0.f;
-            EOFA_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-            if (ms < best_ms) {
-                best_ms = ms;
-                best = c * 4 + spt;
-            }
+    for (int cfg : cands) {
+        auto run = [&]() {
+            if (cfg & CFG_BULK)
+                launch_bulk<P>(kb, ctx, g, cfg & 0xff, (cfg >> 8) & 0xf, hasop, par, in, out, gauge, op, y, a_out,
+                               b_in, red, slot, st);
+            else
+                launch_with(k1, ctx, g, cfg / 4, 1, elem, hasop, par, in, out, gauge, op, y, a_out, b_in, red, slot,
+                            st);
+        };
+        run();  // warm
+        EOFA_CUDA(cudaEventRecord(e0, st));
+        for (int r = 0; r < 3; r++) run();
+        EOFA_CUDA(cudaEventRecord(e1, st));
+        EOFA_CUDA(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        EOFA_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        if (getenv("EOFA_TUNE_LOG")) fprintf(stderr, "dslash tune key %lld: %s %.4f ms\n", key, cfg_str(cfg).c_str(), ms / 3);
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = cfg;
         }
     }
     EOFA_CUDA(cudaEventDestroy(e0));
     EOFA_CUDA(cudaEventDestroy(e1));
     EOFA_CUDA(cudaGetLastError());
+    if (getenv("EOFA_TUNE_LOG")) fprintf(stderr, "dslash tune key %lld: best %s\n", key, cfg_str(best).c_str());
     (*ctx->tuned)[key] = best;
     return best;
 }
 
+// Two slices per thread (SPT = 2) was measured slower than one in every tile
+// shape at 24^3 x 64 x 24 (0.79 vs 0.69 ms, FP32 hop), so only SPT = 1 is built.
 template <int P, int DAG, int LS>
 void launch_dslash_t(const eofa_ctx* ctx, int par, const void* in, void* out, const Op5& op, const void* y,
                      double a_out, double b_in, double* red, int slot, cudaStream_t st) {
@@ -637,18 +702,19 @@ void launch_dslash_t(const eofa_ctx* ctx, int par, const void* in, void* out, co
     Geom g = ctx_geom(ctx);
     const void* gauge = ctx->gauge[P == P64 ? P64 : P32];
     const bool hasop = op.inv[0] || op.inv[1] || op.fwd[0] || op.fwd[1] || op.sigma[0] != 0.0 || op.sigma[1] != 0.0;
-    // two slices per thread (SPT = 2) was measured slower than one in every
-    // tile shape at 24^3 x 64 x 24 (0.79 vs 0.69 ms, FP32 hop); only SPT = 1 is built
-    constexpr bool SPT2 = false;
-    constexpr int S2 = SPT2 ? 2 : 1;
     auto k1 = hasop ? dslash_kernel<P, DAG, LS, true, 1> : dslash_kernel<P, DAG, LS, false, 1>;
-    auto k2 = hasop ? dslash_kernel<P, DAG, LS, true, S2> : dslash_kernel<P, DAG, LS, false, S2>;
+    auto kb = hasop ? dslash_bulk_kernel<P, DAG, LS, true> : dslash_bulk_kernel<P, DAG, LS, false>;
     const long long key = ((((long long)P * 2 + DAG) * 128 + g.Ls) * 2 + (hasop ? 1 : 0)) * 2 + (y ? 1 : 0);
-    const int cfg = tuned_cfg(k1, k2, SPT2, ctx, g, key, pick_ns(g.Ls, sizeof(cpx<R>)), sizeof(cpx<R>), hasop, par, in,
-                              out, gauge, op, y, a_out, b_in, red, slot, st);
-    const int NS = cfg / 4, spt = cfg % 4;
-    if (spt == 2) launch_with(k2, ctx, g, NS, 2, sizeof(cpx<R>), hasop, par, in, out, gauge, op, y, a_out, b_in, red, slot, st);
-    else launch_with(k1, ctx, g, NS, 1, sizeof(cpx<R>), hasop, par, in, out, gauge, op, y, a_out, b_in, red, slot, st);
+    const int ns0 = pick_ns(g.Ls, sizeof(cpx<R>));
+    int cfg = tuned_cfg<P>(k1, kb, ctx, g, key, ns0, sizeof(cpx<R>), hasop, par, in, out, gauge, op, y, a_out, b_in,
+                           red, slot, st);
+    if ((cfg & CFG_BULK) && !bulk_fits<P>(g, cfg & 0xff, (cfg >> 8) & 0xf, hasop, in, y)) cfg = ns0 * 4 + 1;
+    if (cfg & CFG_BULK)
+        launch_bulk<P>(kb, ctx, g, cfg & 0xff, (cfg >> 8) & 0xf, hasop, par, in, out, gauge, op, y, a_out, b_in, red,
+                       slot, st);
+    else
+        launch_with(k1, ctx, g, cfg / 4, 1, sizeof(cpx<R>), hasop, par, in, out, gauge, op, y, a_out, b_in, red, slot,
+                    st);
     EOFA_LAUNCHED();
 }
 

@@ -9,12 +9,14 @@
 //   SC_DELTA             delta = |A p|^2
 //   [128, 1344), 1344    partials and ticket of the generic reductions
 //   [RED_PART, +RED_MAX_BLOCKS), RED_TICKET   partials and ticket of the fused kernels
+//   RED_ERRWORD          device error word (bounded waits that ran out)
 #define SC_RRH 64
 #define SC_GAMMA 96
 #define SC_DELTA 98
 #define RED_PART 2048
 #define RED_MAX_BLOCKS 4096
 #define RED_TICKET (RED_PART + RED_MAX_BLOCKS)
+#define RED_ERRWORD (RED_TICKET + 2)  // int: nonzero after a device wait timed out
 #define RED_TOTAL_DOUBLES (RED_TICKET + 8)
 
 // out = a_out * (-1/2) B[hop(in)] + b_in * y ; |out|^2 -> red[slot] if red
@@ -28,3 +30,6 @@ void fused_local5(const eofa_ctx* ctx, int prec, const Op5& op, const void* x, c
 void fused_xp_update(const eofa_ctx* ctx, int prec, int precx, const double* sc, int it, void* x, void* p,
                      const void* s, cudaStream_t st);
 Op5 op_identity();
+
+// throws EOFA_ETIMEOUT (and clears the word) when a kernel's bounded wait ran out
+void check_device_error(const eofa_ctx* ctx, cudaStream_t st);

@@ -218,6 +218,7 @@ void Solve::check_value(double rr, cudaStream_t st) {
 }
 
 bool Solve::finish(double* x_dev, cudaStream_t st) {
+    check_device_error(ctx, st);
     if (trivial) {
         EOFA_CUDA(cudaMemsetAsync(x_dev, 0, (size_t)ctx->V * ctx->Ls * 12 * 16, st));
         true_rel = 0.0;

@@ -60,6 +60,25 @@ def test_dwf_solve_matches_oracle_solution(eofa):
     assert _rel(x, xo) < 1e-10
 
 
+@pytest.mark.parametrize("cfg", ["5,1,2", "2,1,3"])
+def test_solves_with_staged_dslash(eofa, cfg, monkeypatch):
+    """The staged (bulk-copy) dslash, forced for every launch including the
+    solver's fused axpy form, gives the oracle's D_DWF solution in FP64 and
+    a converged mixed-precision EOFA solve (ragged last tile at NS = 5)."""
+    monkeypatch.setenv("EOFA_DSLASH_CONFIG", cfg)
+    dims, Ls = (4, 4, 2, 4), 8
+    lat, U = _setup(eofa, dims, Ls, eps=0.5)
+    b = inputs.fermion5d(dims, Ls, 6)
+    x, info = lat.solve(b, system=eofa.SYS_DWF, alpha=ALPHA, M5=M5, mf=0.1, tol=1e-13)
+    xo, it, res = osolve.cgnr(lambda v: dwf.dwf(U, v, ALPHA, M5, 0.1, -1),
+                              lambda v: dwf.dwf_dag(U, v, ALPHA, M5, 0.1, -1), b, tol=1e-13)
+    assert _rel(x, xo) < 1e-10
+    x, info = lat.solve(b, system=1, alpha=ALPHA, M5=M5, m1=M1, m2=M2, shift=-0.3, precision=1, tol=1e-10)
+    Ax = oeofa.system_apply(U, x, ALPHA, M5, M1, M2, "L", -0.3, -1)
+    assert np.linalg.norm(b - Ax) / np.linalg.norm(b) < 2e-10
+    assert info.reliable_updates >= 1
+
+
 def test_dwf_solve_warm_start(eofa):
     dims, Ls = (4, 4, 4, 4), 8
     lat, U = _setup(eofa, dims, Ls)
