@@ -220,6 +220,54 @@ int eofa_heatbath_dev(eofa_ctx* ctx, int Ls, double alpha, double M5, double m1,
                       double tol, int npoles, double alpha0, const double* alphas, const double* betas,
                       const double* eta_dev, double* phi_dev, int forecast, eofa_solve_info* info, void* stream);
 
+/* Wilson plaquette gauge action (the gauge part of the HMC runs of Sec. 5;
+ * the paper's Iwasaki / DSDR actions are not reproduced):
+ *   S_g = (beta / 3) sum_{x, mu < nu} Re tr (1 - U_mu(x) U_nu(x+mu) U_mu(x+nu)^+ U_nu(x)^+)
+ * on canonical links U_dev (device, 4 V 3x3; NULL = the context's links),
+ * periodic in every direction.  S (host) gets the value; synchronous. */
+int eofa_gauge_action_dev(eofa_ctx* ctx, double beta, const double* U_dev, double* S, void* stream);
+
+/* Gauge force F_mu(x) = sum_a T^a dS_g/dw^a for U_mu(x) -> exp(i w T^a) U_mu(x)
+ * (the convention of eofa_force), traceless Hermitian, canonical 4 V 3x3 on
+ * the device; accumulate = 1 adds it to F_dev, 0 overwrites. */
+int eofa_gauge_force_dev(eofa_ctx* ctx, double beta, const double* U_dev, double* F_dev, int accumulate,
+                         void* stream);
+
+/* HMC molecular-dynamics trajectory (Sec. 5) for
+ * H = sum_links tr P^2 + S_g(beta) + S_EOFA(phi) with U <- exp(i h P) U and
+ * P <- P - h F.  Integrators: leapfrog; the fourth-order force-gradient
+ * schemes PQPQP = P(h/6) Q(h/2) P~(2h/3) Q(h/2) P(h/6) and
+ * QPQPQ = Q(lam h) P~(h/2) Q((1-2 lam) h) P~(h/2) Q(lam h), lam = 1/2 - sqrt(3)/6,
+ * where P~ kicks with the force at exp(-i z F(U)) U, z = h^2/24 (PQPQP) or
+ * (2 - sqrt 3) h^2/12 (QPQPQ).  n_inner > 0 nests the gauge force: the EOFA
+ * force sits on the outer level and every outer drift is n_inner steps of
+ * the same scheme for S_g.  phi_dev = NULL integrates the gauge action alone
+ * (n_inner must then be 0); beta = 0 drops the gauge action (n_inner 0). */
+#define EOFA_INT_LEAPFROG 0
+#define EOFA_INT_FG_PQPQP 1
+#define EOFA_INT_FG_QPQPQ 2
+typedef struct {
+    int Ls;
+    double alpha, M5, m1, m2;
+    int precision;   /* of the solves, EOFA_PREC_* */
+    double tol;
+    double beta;     /* Wilson gauge coupling */
+    int integrator;  /* EOFA_INT_* */
+    int nsteps;      /* outer steps */
+    double tau;      /* trajectory length */
+    int n_inner;     /* gauge steps per outer drift (0: one level) */
+} eofa_md_params;
+typedef struct {
+    double H0, dH;  /* H at the start, H(end) - H(start) */
+    double kinetic0, kinetic1, S_gauge0, S_gauge1, S_eofa0, S_eofa1;
+    int fermion_forces, gauge_forces, solver_iters;
+} eofa_md_info;
+/* P_dev (4 V traceless Hermitian 3x3, canonical, device) is updated in place;
+ * the context's links end at U(tau) and are copied to U_dev if not NULL.
+ * info: energies, force evaluations and total solver iterations. */
+int eofa_hmc_trajectory_dev(eofa_ctx* ctx, const eofa_md_params* p, const double* phi_dev, double* P_dev,
+                            double* U_dev, eofa_md_info* info, void* stream);
+
 /* Molecular dynamics link update U <- exp(i eps P) U on the device gauge
  * field of the context and on the canonical copy U_dev (if not NULL);
  * P: 4 V traceless Hermitian 3x3, canonical, device. */

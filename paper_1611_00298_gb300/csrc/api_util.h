@@ -17,3 +17,7 @@ int solve_dev_impl(eofa_ctx* ctx, const eofa_solve_params* p, const double* b_de
 
 // Omega_chi P_chi phi: 4D canonical phi -> 5D canonical out (Omega on the device, Ls values)
 void eofa_embed(eofa_ctx* ctx, const double* phi, const double* Om_dev, int chi, double* out, cudaStream_t st);
+
+// gauge action (host value, synchronous) and force (= or += into F) on canonical links (gauge.cu)
+double gauge_action_now(eofa_ctx* ctx, const double* U, double beta, cudaStream_t st);
+void gauge_force_launch(eofa_ctx* ctx, const double* U, double beta, int accumulate, double* F, cudaStream_t st);

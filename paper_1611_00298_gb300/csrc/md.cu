@@ -81,4 +81,142 @@ int eofa_leapfrog_dev(eofa_ctx* ctx, int Ls, double alpha, double M5, double m1,
     return EOFA_OK;
 }
 
+// ---------------------------------------------------------------- force-gradient HMC trajectory
+//
+// H = sum tr P^2 + S_g (Wilson plaquette, beta) + S_EOFA (Eq. (5)), with the
+// fourth-order force-gradient integrators (Sec. 5 runs a nested QPQPQ one):
+//   PQPQP:  P(h/6) Q(h/2) P~(2h/3) Q(h/2) P(h/6)
+//   QPQPQ:  Q(lam h) P~(h/2) Q((1 - 2 lam) h) P~(h/2) Q(lam h),  lam = 1/2 - sqrt(3)/6
+// P~(c) is a kick with the force at the displaced links U' = exp(-i z F(U)) U
+// (z = h^2/24, PQPQP; (2 - sqrt 3) h^2/12, QPQPQ): to first order in z it is
+// the force-gradient correction.  With n_inner > 0 the fermion force is on
+// the outer level and every outer drift Q(t) is n_inner steps of the same
+// scheme for the gauge action (the displacement of a level uses that level's
+// force only).  Leapfrog: P(h/2) Q(h) P(h/2).
+struct Trajectory {
+    eofa_ctx* ctx;
+    const eofa_md_params& p;
+    const double* phi;
+    double* P;
+    cudaStream_t st;
+    long long nP;
+    double *F, *Fz, *Uc, *Usave;
+    int nferm = 0, ngauge = 0, iters = 0;
+
+    Trajectory(eofa_ctx* c, const eofa_md_params& pp, const double* ph, double* Pd, cudaStream_t s)
+        : ctx(c), p(pp), phi(ph), P(Pd), st(s) {
+        nP = 4LL * ctx->V * 9;
+        F = (double*)ctx_buffer(ctx, "md_F", (size_t)nP * 16);
+        Fz = (double*)ctx_buffer(ctx, "md_Fz", (size_t)nP * 16);
+        Usave = (double*)ctx_buffer(ctx, "md_Usave", (size_t)nP * 16);
+        Uc = (double*)ctx_buffer(ctx, "U", 0);
+    }
+    bool nested() const { return p.n_inner > 0; }
+    // force of one level into out: outer = fermion (+ gauge on one level), inner = gauge
+    void force(bool outer, double* out) {
+        if (outer && phi) {
+            eofa_solve_info info[2];
+            int rc = eofa_force_dev(ctx, p.Ls, p.alpha, p.M5, p.m1, p.m2, p.precision, p.tol, phi, out, nullptr, info,
+                                    st);
+            if (rc != EOFA_OK) throw eofa_error(rc, "force evaluation failed in the trajectory: " + ctx->err);
+            nferm++;
+            iters += info[0].iters + info[1].iters;
+            if (!nested() && p.beta != 0.0) {
+                gauge_force_launch(ctx, Uc, p.beta, 1, out, st);
+                ngauge++;
+            }
+        } else {
+            gauge_force_launch(ctx, Uc, p.beta, 0, out, st);
+            ngauge++;
+        }
+    }
+    void links(double eps, const double* Q) {
+        int rc = eofa_link_update_dev(ctx, eps, Q, nullptr, st);
+        if (rc != EOFA_OK) throw eofa_error(rc, ctx->err);
+    }
+    // P <- P - c F(U'), U' = exp(-i z F(U)) U
+    void kick(bool outer, double c, double z) {
+        if (z != 0.0) {
+            force(outer, Fz);
+            EOFA_CUDA(cudaMemcpyAsync(Usave, Uc, (size_t)nP * 16, cudaMemcpyDeviceToDevice, st));
+            links(-z, Fz);
+            force(outer, F);
+            EOFA_CUDA(cudaMemcpyAsync(Uc, Usave, (size_t)nP * 16, cudaMemcpyDeviceToDevice, st));
+            launch_gauge_pack(ctx, Uc, st);
+        } else {
+            force(outer, F);
+        }
+        mom_update_kernel<<<nblk(nP, 256), 256, 0, st>>>(nP, c, (const double2*)F, (double2*)P);
+        EOFA_LAUNCHED();
+    }
+    void drift(bool outer, double t) {
+        if (outer && nested()) steps(false, t, p.n_inner);
+        else links(t, P);
+    }
+    void steps(bool outer, double t, int n) {
+        const double h = t / n;
+        for (int k = 0; k < n; k++) {
+            if (p.integrator == EOFA_INT_FG_PQPQP) {
+                kick(outer, h / 6, 0.0);
+                drift(outer, h / 2);
+                kick(outer, 2 * h / 3, h * h / 24);
+                drift(outer, h / 2);
+                kick(outer, h / 6, 0.0);
+            } else if (p.integrator == EOFA_INT_FG_QPQPQ) {
+                const double lam = 0.5 - std::sqrt(3.0) / 6.0, z = (2.0 - std::sqrt(3.0)) / 12.0 * h * h;
+                drift(outer, lam * h);
+                kick(outer, h / 2, z);
+                drift(outer, (1 - 2 * lam) * h);
+                kick(outer, h / 2, z);
+                drift(outer, lam * h);
+            } else {
+                kick(outer, h / 2, 0.0);
+                drift(outer, h);
+                kick(outer, h / 2, 0.0);
+            }
+        }
+    }
+    void energy(double* K, double* Sg, double* Sf) {
+        blas_flat_dot(ctx, nP, P, P, 12, st);
+        *K = red_fetch(ctx, 12, st);
+        *Sg = p.beta != 0.0 ? gauge_action_now(ctx, Uc, p.beta, st) : 0.0;
+        *Sf = 0.0;
+        if (phi) {
+            eofa_solve_info info[2];
+            int rc = eofa_action_dev(ctx, p.Ls, p.alpha, p.M5, p.m1, p.m2, p.precision, p.tol, phi, Sf, info, st);
+            if (rc != EOFA_OK) throw eofa_error(rc, "action failed in the trajectory: " + ctx->err);
+            iters += info[0].iters + info[1].iters;
+        }
+    }
+};
+
+extern "C" int eofa_hmc_trajectory_dev(eofa_ctx* ctx, const eofa_md_params* p, const double* phi_dev, double* P_dev,
+                                       double* U_dev, eofa_md_info* info, void* stream) {
+    if (!ctx || !p || !P_dev || !info) return fail(ctx, EOFA_EINVAL, "null argument");
+    if (p->nsteps < 1 || !(p->tau > 0) || p->n_inner < 0 || p->integrator < EOFA_INT_LEAPFROG ||
+        p->integrator > EOFA_INT_FG_QPQPQ || (p->n_inner > 0 && (!phi_dev || p->beta == 0.0)) ||
+        (!phi_dev && p->beta == 0.0))
+        return fail(ctx, EOFA_EINVAL, "bad trajectory parameters");
+    cudaStream_t st = (cudaStream_t)stream;
+    try {
+        require_gauge(ctx);
+        Trajectory T(ctx, *p, phi_dev, P_dev, st);
+        eofa_md_info r{};
+        T.energy(&r.kinetic0, &r.S_gauge0, &r.S_eofa0);
+        T.steps(true, p->tau, p->nsteps);
+        T.energy(&r.kinetic1, &r.S_gauge1, &r.S_eofa1);
+        r.H0 = r.kinetic0 + r.S_gauge0 + r.S_eofa0;
+        r.dH = (r.kinetic1 + r.S_gauge1 + r.S_eofa1) - r.H0;
+        r.fermion_forces = T.nferm;
+        r.gauge_forces = T.ngauge;
+        r.solver_iters = T.iters;
+        if (U_dev) EOFA_CUDA(cudaMemcpyAsync(U_dev, T.Uc, (size_t)T.nP * 16, cudaMemcpyDeviceToDevice, st));
+        EOFA_CUDA(cudaStreamSynchronize(st));
+        *info = r;
+    } catch (const eofa_error& e) {
+        return fail(ctx, e.code, e.msg);
+    }
+    return EOFA_OK;
+}
+
 }  // extern "C"

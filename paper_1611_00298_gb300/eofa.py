@@ -32,7 +32,9 @@ EXPORTS = [
     "eofa_solve_batched", "eofa_kernel_launches", "eofa_profile_start", "eofa_profile_stop",
     "eofa_dwf_apply_noalloc", "eofa_schur_hop_dev", "eofa_pseudofermion_solutions_dev",
     "eofa_set_reliable_delta", "eofa_leapfrog_dev", "eofa_rational_inv_sqrt", "eofa_heatbath_dev",
+    "eofa_gauge_action_dev", "eofa_gauge_force_dev", "eofa_hmc_trajectory_dev",
 ]
+INT_LEAPFROG, INT_FG_PQPQP, INT_FG_QPQPQ = 0, 1, 2
 
 
 class EOFAError(RuntimeError):
@@ -51,6 +53,23 @@ class SolveParams(ctypes.Structure):
 
 class Profile(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_longlong * 6), ("ms", ctypes.c_double * 6)]
+
+
+class MDParams(ctypes.Structure):
+    _fields_ = [("Ls", ctypes.c_int), ("alpha", ctypes.c_double), ("M5", ctypes.c_double), ("m1", ctypes.c_double),
+                ("m2", ctypes.c_double), ("precision", ctypes.c_int), ("tol", ctypes.c_double),
+                ("beta", ctypes.c_double), ("integrator", ctypes.c_int), ("nsteps", ctypes.c_int),
+                ("tau", ctypes.c_double), ("n_inner", ctypes.c_int)]
+
+
+class MDInfo(ctypes.Structure):
+    _fields_ = [("H0", ctypes.c_double), ("dH", ctypes.c_double), ("kinetic0", ctypes.c_double),
+                ("kinetic1", ctypes.c_double), ("S_gauge0", ctypes.c_double), ("S_gauge1", ctypes.c_double),
+                ("S_eofa0", ctypes.c_double), ("S_eofa1", ctypes.c_double), ("fermion_forces", ctypes.c_int),
+                ("gauge_forces", ctypes.c_int), ("solver_iters", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class SolveInfo(ctypes.Structure):
@@ -105,6 +124,9 @@ def load_library(path: str = LIB_PATH):
         "eofa_pseudofermion_solutions_dev": (I, [P, I, D, D, D, D, I, D, P, P, P, ctypes.POINTER(D),
                                                  ctypes.POINTER(SolveInfo), P]),
         "eofa_set_reliable_delta": (I, [P, D]),
+        "eofa_gauge_action_dev": (I, [P, D, P, ctypes.POINTER(D), P]),
+        "eofa_gauge_force_dev": (I, [P, D, P, P, I, P]),
+        "eofa_hmc_trajectory_dev": (I, [P, ctypes.POINTER(MDParams), P, P, P, ctypes.POINTER(MDInfo), P]),
         "eofa_rational_inv_sqrt": (I, [I, D, D, ctypes.POINTER(D), P, P, ctypes.POINTER(D)]),
         "eofa_heatbath_dev": (I, [P, I, D, D, D, D, I, D, I, D, P, P, P, P, I, ctypes.POINTER(SolveInfo), P]),
         "eofa_leapfrog_dev": (I, [P, I, D, D, D, D, I, D, I, D, P, P, P, ctypes.POINTER(D), ctypes.POINTER(D), P]),
@@ -377,6 +399,28 @@ class Lattice:
                                         ctypes.byref(H0), _stream())
         self._check(rc, "leapfrog_dev")
         return dH.value, H0.value
+
+    def gauge_action_dev(self, beta, U=None):
+        """Wilson plaquette action of U (device canonical) or of the context's links."""
+        S = ctypes.c_double()
+        self._check(self.lib.eofa_gauge_action_dev(self.ctx, beta, _ptr(U) if U is not None else None,
+                                                   ctypes.byref(S), _stream()), "gauge_action_dev")
+        return S.value
+
+    def gauge_force_dev(self, beta, F, U=None, accumulate=False):
+        self._check(self.lib.eofa_gauge_force_dev(self.ctx, beta, _ptr(U) if U is not None else None, _ptr(F),
+                                                  int(accumulate), _stream()), "gauge_force_dev")
+
+    def hmc_trajectory_dev(self, P, phi=None, U=None, *, alpha=2.0, M5=1.8, m1=0.04, m2=1.0, precision=PREC_F64,
+                           tol=1e-10, beta=0.0, integrator=INT_FG_QPQPQ, nsteps=4, tau=1.0, n_inner=0):
+        """One MD trajectory (P and the context's links updated in place); returns the info dict."""
+        prm = MDParams(self.Ls, alpha, M5, m1, m2, precision, tol, beta, integrator, nsteps, tau, n_inner)
+        info = MDInfo()
+        rc = self.lib.eofa_hmc_trajectory_dev(self.ctx, ctypes.byref(prm), _ptr(phi) if phi is not None else None,
+                                              _ptr(P), _ptr(U) if U is not None else None, ctypes.byref(info),
+                                              _stream())
+        self._check(rc, "hmc_trajectory_dev")
+        return info.as_dict()
 
     def link_update_dev(self, eps, P, U=None):
         self._check(self.lib.eofa_link_update_dev(self.ctx, eps, _ptr(P), _ptr(U) if U is not None else None,

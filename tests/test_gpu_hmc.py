@@ -1,0 +1,125 @@
+"""GPU gauge action / force and force-gradient HMC trajectories (Sec. 5)
+against the oracle, plus the fourth-order dH scaling and reversibility of the
+device integrator."""
+import numpy as np
+import pytest
+
+from oracle import gauge
+from paper_1611_00298_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+ALPHA, M5, M1, M2, BETA = 2.0, 1.8, 0.04, 1.0, 5.7
+
+
+@pytest.fixture(scope="module")
+def eofa():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1611_00298_gb300 import eofa as e
+    e.load_library()
+    return e
+
+
+def _dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def test_gauge_action_and_force_match_oracle(eofa):
+    import torch
+    dims = (4, 4, 2, 6)
+    U = inputs.gauge_field(dims, 0.6, 3)
+    lat = eofa.Lattice(dims, 4)
+    lat.gauge_load(U)
+    S = lat.gauge_action_dev(BETA)
+    assert S == pytest.approx(gauge.action(U, BETA), rel=1e-13)
+    F = torch.empty(U.shape, dtype=torch.complex128, device="cuda")
+    lat.gauge_force_dev(BETA, F, U=_dev(U))
+    Fo = gauge.force(U, BETA)
+    assert np.abs(F.cpu().numpy() - Fo).max() < 1e-12 * np.abs(Fo).max()
+    lat.gauge_force_dev(BETA, F, accumulate=True)
+    torch.cuda.synchronize()
+    assert np.abs(F.cpu().numpy() - 2 * Fo).max() < 1e-12 * np.abs(Fo).max()
+    lat.close()
+
+
+@pytest.mark.parametrize("integrator,scheme", [(0, "leapfrog"), (1, "pqpqp"), (2, "qpqpq")])
+def test_pure_gauge_trajectory_matches_oracle(eofa, integrator, scheme):
+    import torch
+    dims = (4, 4, 2, 4)
+    U = inputs.gauge_field(dims, 0.5, 5)
+    P = inputs.momenta(dims, 6)
+    lat = eofa.Lattice(dims, 4)
+    lat.gauge_load(U)
+    Pd = _dev(P)
+    Ud = torch.empty_like(Pd)
+    info = lat.hmc_trajectory_dev(Pd, None, Ud, beta=BETA, integrator=integrator, nsteps=3, tau=0.6)
+    U1, P1, dH = gauge.trajectory(U, P, gauge.Forces(BETA), 0.6, 3, scheme)
+    assert np.abs(Ud.cpu().numpy() - U1).max() < 1e-11
+    assert np.abs(Pd.cpu().numpy() - P1).max() < 1e-10
+    assert info["dH"] == pytest.approx(dH, abs=1e-9)
+    lat.close()
+
+
+def test_nested_eofa_trajectory_matches_oracle(eofa):
+    """EOFA force on the outer level, gauge force nested (2 inner steps), QPQPQ."""
+    import torch
+    dims, Ls = (2, 2, 2, 2), 4
+    U = inputs.gauge_field(dims, 0.4, 7)
+    P = inputs.momenta(dims, 8)
+    phi = inputs.fermion4d(dims, 9)
+    lat = eofa.Lattice(dims, Ls)
+    lat.gauge_load(U)
+    Pd, phid = _dev(P), _dev(phi)
+    Ud = torch.empty_like(Pd)
+    info = lat.hmc_trajectory_dev(Pd, phid, Ud, alpha=ALPHA, M5=M5, m1=M1, m2=M2, tol=1e-13, beta=BETA,
+                                  integrator=eofa.INT_FG_QPQPQ, nsteps=2, tau=0.5, n_inner=2)
+    f = gauge.Forces(BETA, dict(phi=phi, Ls=Ls, alpha=ALPHA, M5=M5, m1=M1, m2=M2, bc_t=-1.0, tol=1e-13))
+    U1, P1, dH = gauge.trajectory(U, P, f, 0.5, 2, "qpqpq", n_inner=2)
+    assert info["fermion_forces"] == f.n_fermion == 8
+    assert np.abs(Ud.cpu().numpy() - U1).max() < 1e-10
+    assert np.abs(Pd.cpu().numpy() - P1).max() < 1e-9
+    assert info["dH"] == pytest.approx(dH, abs=1e-8)
+    lat.close()
+
+
+def test_force_gradient_fourth_order_and_reversible(eofa):
+    """dH(h) / dH(h/2) ~ 16 for the nested QPQPQ force-gradient trajectory with
+    EOFA + gauge forces; integrating back with -P recovers U and P."""
+    import torch
+    dims, Ls = (4, 4, 4, 4), 8
+    U = inputs.gauge_field(dims, 0.3, 11)
+    P = inputs.momenta(dims, 12)
+    phi = inputs.fermion4d(dims, 13)
+    kw = dict(alpha=ALPHA, M5=M5, m1=M1, m2=M2, tol=1e-13, beta=BETA, integrator=eofa.INT_FG_QPQPQ, tau=0.5,
+              n_inner=2)
+    lat = eofa.Lattice(dims, Ls)
+    dHs = []
+    for n in (2, 4):
+        lat.gauge_load(U)
+        Pd = _dev(P)
+        dHs.append(lat.hmc_trajectory_dev(Pd, _dev(phi), None, nsteps=n, **kw)["dH"])
+    assert abs(dHs[0] / dHs[1]) == pytest.approx(16, rel=0.3), dHs
+    lat.gauge_load(U)
+    Pd = _dev(P)
+    Ud = torch.empty_like(Pd)
+    lat.hmc_trajectory_dev(Pd, _dev(phi), Ud, nsteps=2, **kw)
+    Pd.neg_()
+    lat.hmc_trajectory_dev(Pd, _dev(phi), Ud, nsteps=2, **kw)
+    assert np.abs(Ud.cpu().numpy() - U).max() < 1e-9
+    assert np.abs(Pd.cpu().numpy() + P).max() < 1e-8
+    lat.close()
+
+
+def test_trajectory_rejects_bad_parameters(eofa):
+    dims = (2, 2, 2, 2)
+    lat = eofa.Lattice(dims, 4)
+    lat.gauge_load(inputs.gauge_field(dims, 0.3, 1))
+    Pd = _dev(inputs.momenta(dims, 2))
+    with pytest.raises(eofa.EOFAError):
+        lat.hmc_trajectory_dev(Pd, None, None, beta=0.0)  # nothing to integrate
+    with pytest.raises(eofa.EOFAError):
+        lat.hmc_trajectory_dev(Pd, None, None, beta=BETA, n_inner=2)  # nesting needs a fermion level
+    lat.close()
