@@ -169,6 +169,16 @@ int eofa_force_dev(eofa_ctx* ctx, int Ls, double alpha, double M5, double m1, do
 int eofa_force_from_chi_dev(eofa_ctx* ctx, double k, const double* chiL_dev,
                             const double* chiR_dev, double* F_dev, void* stream);
 
+/* The two terms of Eq. (7) separately (asymmetric integration of the L and
+ * R parts, Sec. 3.3): FL_dev gets the force of S_L = phi_-^+ M_L phi_- (one
+ * solve for chi_L), FR_dev that of S_R = phi_+^+ M_R phi_+ (one solve for
+ * chi_R); either may be NULL (its solve is skipped).  Same layout and
+ * convention as eofa_force_dev; FL + FR = F.  info[0] / info[1]: the solves
+ * (zeroed when skipped). */
+int eofa_force_parts_dev(eofa_ctx* ctx, int Ls, double alpha, double M5, double m1, double m2, int precision,
+                         double tol, const double* phi_dev, double* FL_dev, double* FR_dev, eofa_solve_info info[2],
+                         void* stream);
+
 /* Gradient of S with respect to the real and imaginary parts of every link
  * entry (for automatic differentiation): G has the gauge layout and holds
  * dS/dRe U + i dS/dIm U.  Uses the same chi_L, chi_R as the force. */
@@ -241,8 +251,12 @@ int eofa_gauge_force_dev(eofa_ctx* ctx, double beta, const double* U_dev, double
  * where P~ kicks with the force at exp(-i z F(U)) U, z = h^2/24 (PQPQP) or
  * (2 - sqrt 3) h^2/12 (QPQPQ).  n_inner > 0 nests the gauge force: the EOFA
  * force sits on the outer level and every outer drift is n_inner steps of
- * the same scheme for S_g.  phi_dev = NULL integrates the gauge action alone
- * (n_inner must then be 0); beta = 0 drops the gauge action (n_inner 0). */
+ * the same scheme for S_g.  split_lr = 1 integrates the two terms of Eq. (5)
+ * on separate time scales (Sexton-Weingarten): the S_R force on the outer
+ * level, the S_L force with n_middle steps per outer drift, the gauge force
+ * with n_inner steps per S_L drift (beta = 0: no gauge level).  phi_dev =
+ * NULL integrates the gauge action alone (n_inner must then be 0); beta = 0
+ * drops the gauge action. */
 #define EOFA_INT_LEAPFROG 0
 #define EOFA_INT_FG_PQPQP 1
 #define EOFA_INT_FG_QPQPQ 2
@@ -255,7 +269,9 @@ typedef struct {
     int integrator;  /* EOFA_INT_* */
     int nsteps;      /* outer steps */
     double tau;      /* trajectory length */
-    int n_inner;     /* gauge steps per outer drift (0: one level) */
+    int n_inner;     /* gauge steps per drift of the level above (0: one level) */
+    int split_lr;    /* 1: S_R force outermost, S_L force in the middle (Sec. 3.3 asymmetry) */
+    int n_middle;    /* with split_lr: S_L steps per outer drift */
 } eofa_md_params;
 typedef struct {
     double H0, dH;  /* H at the start, H(end) - H(start) */

@@ -134,6 +134,18 @@ def action(U, phi, Ls, alpha, M5, m1, m2, bc_t, tol=1e-12, chis=None):
     return S
 
 
+def partial_actions(U, phi, Ls, alpha, M5, m1, m2, bc_t, tol=1e-12):
+    """(S_L, S_R), the two terms of Eq. (5): S_L = phi_-^+ M_L phi_- (P_- part,
+    through chi_L) and S_R = phi_+^+ M_R phi_+ (P_+ part, through chi_R)."""
+    Op, Om = omega(Ls, alpha)
+    k = k_coefficient(Ls, alpha, m1, m2)
+    chiL, chiR, _ = pseudofermion_solutions(U, phi, Ls, alpha, M5, m1, m2, bc_t, tol)
+    pm, pp = dwf.spin_mul(dwf.P_MINUS, phi), dwf.spin_mul(dwf.P_PLUS, phi)
+    SL = norm2(pm) - k * complex(np.vdot(embed(phi, Om, -1), chiL)).real
+    SR = norm2(pp) + k * complex(np.vdot(embed(phi, Op, +1), chiR)).real
+    return SL, SR
+
+
 # ---------------------------------------------------------------- Eq. (7)
 
 def force_from_chi(U, chiL, chiR, k, bc_t):
@@ -172,6 +184,18 @@ def force(U, phi, Ls, alpha, M5, m1, m2, bc_t, tol=1e-12):
     chiL, chiR, _ = pseudofermion_solutions(U, phi, Ls, alpha, M5, m1, m2, bc_t, tol)
     k = k_coefficient(Ls, alpha, m1, m2)
     return force_from_chi(U, chiL, chiR, k, bc_t)[0]
+
+
+def force_part(U, phi, Ls, alpha, M5, m1, m2, bc_t, part, tol=1e-12):
+    """The force of S_L (part 'L', one solve for chi_L) or of S_R (part 'R',
+    one solve for chi_R): the two terms of Eq. (7) separately."""
+    Op, Om = omega(Ls, alpha)
+    k = k_coefficient(Ls, alpha, m1, m2)
+    if part == "L":
+        chi, _, _ = system_solve(U, embed(phi, Om, -1), alpha, M5, m1, m2, "L", 0.0, bc_t, tol)
+        return force_from_chi(U, chi, np.zeros_like(chi), k, bc_t)[0]
+    chi, _, _ = system_solve(U, embed(phi, Op, +1), alpha, M5, m1, m2, "R", -1.0, bc_t, tol)
+    return force_from_chi(U, np.zeros_like(chi), chi, k, bc_t)[0]
 
 
 def force_components(F):

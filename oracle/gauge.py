@@ -130,30 +130,49 @@ def _kick(U, P, c, z, force_fn):
     return P - c * force_fn(link_update(U, -z * force_fn(U)))
 
 
-def _steps(U, P, t, nsteps, scheme, force_fn, drift):
-    """nsteps force-gradient steps of length h = t / nsteps; drift(U, P, t) moves U."""
-    h = t / nsteps
-    for _ in range(nsteps):
+def _level_steps(U, P, t, levels, scheme):
+    """levels[0] = (force, n): n steps of length t / n of the scheme with that
+    force; each drift is the next level's integration (a link update at the
+    innermost level)."""
+    force_fn, n = levels[0]
+    rest = levels[1:]
+
+    def drift(U_, P_, dt):
+        if rest:
+            return _level_steps(U_, P_, dt, rest, scheme)
+        return link_update(U_, dt * P_), P_
+
+    h = t / n
+    for _ in range(n):
         if scheme == "pqpqp":
             P = _kick(U, P, h / 6, 0.0, force_fn)
-            U = drift(U, P, h / 2)
+            U, P = drift(U, P, h / 2)
             P = _kick(U, P, 2 * h / 3, Z_PQPQP * h * h, force_fn)
-            U = drift(U, P, h / 2)
+            U, P = drift(U, P, h / 2)
             P = _kick(U, P, h / 6, 0.0, force_fn)
         elif scheme == "qpqpq":
             lam = LAMBDA_QPQPQ
-            U = drift(U, P, lam * h)
+            U, P = drift(U, P, lam * h)
             P = _kick(U, P, h / 2, Z_QPQPQ * h * h, force_fn)
-            U = drift(U, P, (1 - 2 * lam) * h)
+            U, P = drift(U, P, (1 - 2 * lam) * h)
             P = _kick(U, P, h / 2, Z_QPQPQ * h * h, force_fn)
-            U = drift(U, P, lam * h)
+            U, P = drift(U, P, lam * h)
         elif scheme == "leapfrog":
             P = _kick(U, P, h / 2, 0.0, force_fn)
-            U = drift(U, P, h)
+            U, P = drift(U, P, h)
             P = _kick(U, P, h / 2, 0.0, force_fn)
         else:
             raise ValueError(scheme)
     return U, P
+
+
+def trajectory_levels(U, P, levels, energy, tau, scheme="qpqpq"):
+    """Multi-time-scale trajectory: levels = [(force_fn, n), ...], outermost
+    first (n = outer steps, then steps per drift of the level above);
+    energy(U, P) = H.  Returns (U', P', dH)."""
+    H0 = energy(U, P)
+    U1, P1 = _level_steps(U, P, tau, levels, scheme)
+    return U1, P1, energy(U1, P1) - H0
 
 
 def trajectory(U, P, forces, tau, nsteps, scheme="qpqpq", n_inner=0):
@@ -163,43 +182,24 @@ def trajectory(U, P, forces, tau, nsteps, scheme="qpqpq", n_inner=0):
     force: every drift of the outer (fermion) level is n_inner steps of the
     same scheme for the gauge action alone.
     """
-    H0 = forces.energy(U, P)
-    plain = lambda U_, P_, t: link_update(U_, t * P_)  # noqa: E731
     if n_inner == 0:
         def both(U_):
             return forces.outer(U_) + (forces.inner(U_) if forces.fermion is not None else 0.0)
-        U1, P1 = _steps(U, P, tau, nsteps, scheme, both, plain)
+        levels = [(both, nsteps)]
     else:
-        def inner_drift(U_, P_, t):
-            return _steps(U_, P_, t, n_inner, scheme, forces.inner, plain)
-        U1, P1 = U, P
-        h = tau / nsteps
-        for _ in range(nsteps):
-            U1, P1 = _nested_step(U1, P1, h, scheme, forces.outer, inner_drift)
-    return U1, P1, forces.energy(U1, P1) - H0
+        levels = [(forces.outer, nsteps), (forces.inner, n_inner)]
+    return trajectory_levels(U, P, levels, forces.energy, tau, scheme)
 
 
-def _nested_step(U, P, h, scheme, outer_fn, inner_drift):
-    """One outer step whose drifts are inner integrations (they move U and P)."""
-    def drift(U_, P_, t):
-        return inner_drift(U_, P_, t)
-    if scheme == "pqpqp":
-        P = _kick(U, P, h / 6, 0.0, outer_fn)
-        U, P = drift(U, P, h / 2)
-        P = _kick(U, P, 2 * h / 3, Z_PQPQP * h * h, outer_fn)
-        U, P = drift(U, P, h / 2)
-        P = _kick(U, P, h / 6, 0.0, outer_fn)
-    elif scheme == "qpqpq":
-        lam = LAMBDA_QPQPQ
-        U, P = drift(U, P, lam * h)
-        P = _kick(U, P, h / 2, Z_QPQPQ * h * h, outer_fn)
-        U, P = drift(U, P, (1 - 2 * lam) * h)
-        P = _kick(U, P, h / 2, Z_QPQPQ * h * h, outer_fn)
-        U, P = drift(U, P, lam * h)
-    elif scheme == "leapfrog":
-        P = _kick(U, P, h / 2, 0.0, outer_fn)
-        U, P = drift(U, P, h)
-        P = _kick(U, P, h / 2, 0.0, outer_fn)
-    else:
-        raise ValueError(scheme)
-    return U, P
+def split_lr_trajectory(U, P, beta, fermion, tau, nsteps, n_middle, n_inner, scheme="qpqpq"):
+    """Asymmetric EOFA integration (Sexton-Weingarten over the two terms of
+    Eq. (5)): the P_+ (S_R) force on the outer level, the P_- (S_L) force in
+    the middle, the gauge force innermost (omitted when beta = 0)."""
+    f = fermion
+    args = (f["phi"], f["Ls"], f["alpha"], f["M5"], f["m1"], f["m2"], f["bc_t"])
+    levels = [(lambda U_: oeofa.force_part(U_, *args, "R", f["tol"]), nsteps),
+              (lambda U_: oeofa.force_part(U_, *args, "L", f["tol"]), n_middle)]
+    if beta != 0.0:
+        levels.append((lambda U_: force(U_, beta), n_inner))
+    forces = Forces(beta, fermion)
+    return trajectory_levels(U, P, levels, forces.energy, tau, scheme)

@@ -21,3 +21,7 @@ void eofa_embed(eofa_ctx* ctx, const double* phi, const double* Om_dev, int chi,
 // gauge action (host value, synchronous) and force (= or += into F) on canonical links (gauge.cu)
 double gauge_action_now(eofa_ctx* ctx, const double* U, double beta, cudaStream_t st);
 void gauge_force_launch(eofa_ctx* ctx, const double* U, double beta, int accumulate, double* F, cudaStream_t st);
+
+extern "C" int eofa_force_parts_dev(eofa_ctx* ctx, int Ls, double alpha, double M5, double m1, double m2,
+                                    int precision, double tol, const double* phi_dev, double* FL_dev, double* FR_dev,
+                                    eofa_solve_info info[2], void* stream);

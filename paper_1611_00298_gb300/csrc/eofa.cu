@@ -99,10 +99,23 @@ __global__ void force_kernel(Coords d, int Ls, int bc_t, double k, const double2
     cpx<double> Y[9];
     for (int e = 0; e < 9; e++) Y[e] = mk(0.0, 0.0);
     switch (mu) {
-        case 0: accumulate_Y<0>(chiL, V, Ls, i, ifw, k, Y); accumulate_Y<0>(chiR, V, Ls, i, ifw, -k, Y); break;
-        case 1: accumulate_Y<1>(chiL, V, Ls, i, ifw, k, Y); accumulate_Y<1>(chiR, V, Ls, i, ifw, -k, Y); break;
-        case 2: accumulate_Y<2>(chiL, V, Ls, i, ifw, k, Y); accumulate_Y<2>(chiR, V, Ls, i, ifw, -k, Y); break;
-        default: accumulate_Y<3>(chiL, V, Ls, i, ifw, k, Y); accumulate_Y<3>(chiR, V, Ls, i, ifw, -k, Y); break;
+        // a null chi drops its term (the force of S_L or S_R alone)
+        case 0:
+            if (chiL) accumulate_Y<0>(chiL, V, Ls, i, ifw, k, Y);
+            if (chiR) accumulate_Y<0>(chiR, V, Ls, i, ifw, -k, Y);
+            break;
+        case 1:
+            if (chiL) accumulate_Y<1>(chiL, V, Ls, i, ifw, k, Y);
+            if (chiR) accumulate_Y<1>(chiR, V, Ls, i, ifw, -k, Y);
+            break;
+        case 2:
+            if (chiL) accumulate_Y<2>(chiL, V, Ls, i, ifw, k, Y);
+            if (chiR) accumulate_Y<2>(chiR, V, Ls, i, ifw, -k, Y);
+            break;
+        default:
+            if (chiL) accumulate_Y<3>(chiL, V, Ls, i, ifw, k, Y);
+            if (chiR) accumulate_Y<3>(chiR, V, Ls, i, ifw, -k, Y);
+            break;
     }
     for (int e = 0; e < 9; e++) Y[e] = phase * Y[e];
     double2* out = F + t * 9;
@@ -185,9 +198,10 @@ struct ChiBufs {
 };
 
 // The two solves behind Eq. (5) and Eq. (7); fills S if requested.
+// parts: 1 = chi_L only, 2 = chi_R only, 3 = both (S needs both).
 ChiBufs eofa_chis(eofa_ctx* ctx, int Ls, double alpha, double M5, double m1, double m2, int precision, double tol,
                   const double* phi_dev, double* S, eofa_solve_info info[2], cudaStream_t st, int* rc_out,
-                  double* chiL_out = nullptr, double* chiR_out = nullptr) {
+                  double* chiL_out = nullptr, double* chiR_out = nullptr, int parts = 3) {
     check_ls(ctx, Ls);
     require_gauge(ctx);
     if (!(m1 < m2)) throw eofa_error(EOFA_EINVAL, "EOFA needs m1 < m2 (k > 0)");
@@ -222,12 +236,14 @@ ChiBufs eofa_chis(eofa_ctx* ctx, int Ls, double alpha, double M5, double m1, dou
     p.use_x0 = 0;
     p.system = EOFA_SYS_EOFA_L;
     p.shift = 0.0;
-    int rc1 = solve_dev_impl(ctx, &p, c.bL, c.chiL, &info[0], st);
+    int rc1 = EOFA_OK, rc2 = EOFA_OK;
+    info[0] = info[1] = eofa_solve_info{};
+    if (parts & 1) rc1 = solve_dev_impl(ctx, &p, c.bL, c.chiL, &info[0], st);
     p.system = EOFA_SYS_EOFA_R;
     p.shift = -1.0;
-    int rc2 = solve_dev_impl(ctx, &p, c.bR, c.chiR, &info[1], st);
+    if (parts & 2) rc2 = solve_dev_impl(ctx, &p, c.bR, c.chiR, &info[1], st);
     *rc_out = rc1 != EOFA_OK ? rc1 : rc2;
-    if (S) {
+    if (S && parts == 3) {
         double k = eofa_k(Ls, alpha, m1, m2);
         blas_flat_dot(ctx, V * 12, phi_dev, phi_dev, 6, st);
         blas_flat_dot(ctx, n, c.bL, c.chiL, 8, st);
@@ -327,6 +343,28 @@ int eofa_force_dev(eofa_ctx* ctx, int Ls, double alpha, double M5, double m1, do
         int rc = EOFA_OK;
         ChiBufs c = eofa_chis(ctx, Ls, alpha, M5, m1, m2, precision, tol, phi_dev, S, info, st, &rc);
         launch_force(ctx, eofa_k(Ls, alpha, m1, m2), c.chiL, c.chiR, F_dev, 0, st);
+        EOFA_CUDA(cudaStreamSynchronize(st));
+        return rc;
+    } catch (const eofa_error& e) {
+        return fail(ctx, e.code, e.msg);
+    }
+}
+
+int eofa_force_parts_dev(eofa_ctx* ctx, int Ls, double alpha, double M5, double m1, double m2, int precision,
+                         double tol, const double* phi_dev, double* FL_dev, double* FR_dev, eofa_solve_info info[2],
+                         void* stream) {
+    if (!ctx || !phi_dev || (!FL_dev && !FR_dev)) return fail(ctx, EOFA_EINVAL, "null argument");
+    eofa_solve_info loc[2];
+    if (!info) info = loc;
+    cudaStream_t st = (cudaStream_t)stream;
+    try {
+        int rc = EOFA_OK;
+        const int parts = (FL_dev ? 1 : 0) | (FR_dev ? 2 : 0);
+        ChiBufs c = eofa_chis(ctx, Ls, alpha, M5, m1, m2, precision, tol, phi_dev, nullptr, info, st, &rc, nullptr,
+                              nullptr, parts);
+        const double k = eofa_k(Ls, alpha, m1, m2);
+        if (FL_dev) launch_force(ctx, k, c.chiL, nullptr, FL_dev, 0, st);
+        if (FR_dev) launch_force(ctx, k, nullptr, c.chiR, FR_dev, 0, st);
         EOFA_CUDA(cudaStreamSynchronize(st));
         return rc;
     } catch (const eofa_error& e) {

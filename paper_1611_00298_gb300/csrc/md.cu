@@ -4,6 +4,7 @@
 #include "api_util.h"
 
 #include <cmath>
+#include <vector>
 
 namespace {
 
@@ -89,10 +90,16 @@ int eofa_leapfrog_dev(eofa_ctx* ctx, int Ls, double alpha, double M5, double m1,
 //   QPQPQ:  Q(lam h) P~(h/2) Q((1 - 2 lam) h) P~(h/2) Q(lam h),  lam = 1/2 - sqrt(3)/6
 // P~(c) is a kick with the force at the displaced links U' = exp(-i z F(U)) U
 // (z = h^2/24, PQPQP; (2 - sqrt 3) h^2/12, QPQPQ): to first order in z it is
-// the force-gradient correction.  With n_inner > 0 the fermion force is on
-// the outer level and every outer drift Q(t) is n_inner steps of the same
-// scheme for the gauge action (the displacement of a level uses that level's
-// force only).  Leapfrog: P(h/2) Q(h) P(h/2).
+// the force-gradient correction.  Leapfrog: P(h/2) Q(h) P(h/2).
+//
+// Time scales are a list of levels, outermost first; every drift of a level
+// is the next level's integration (a link update at the innermost one), and
+// a level's displacement uses its own force only (the forces commute):
+//   one level:     EOFA + gauge (or gauge alone without phi)
+//   n_inner > 0:   EOFA | gauge
+//   split_lr:      S_R force | S_L force | gauge (asymmetric L/R integration)
+enum Force { F_EOFA_AND_GAUGE, F_EOFA, F_EOFA_L, F_EOFA_R, F_GAUGE };
+
 struct Trajectory {
     eofa_ctx* ctx;
     const eofa_md_params& p;
@@ -101,6 +108,8 @@ struct Trajectory {
     cudaStream_t st;
     long long nP;
     double *F, *Fz, *Uc, *Usave;
+    std::vector<Force> kind;
+    std::vector<int> nsub;
     int nferm = 0, ngauge = 0, iters = 0;
 
     Trajectory(eofa_ctx* c, const eofa_md_params& pp, const double* ph, double* Pd, cudaStream_t s)
@@ -110,23 +119,44 @@ struct Trajectory {
         Fz = (double*)ctx_buffer(ctx, "md_Fz", (size_t)nP * 16);
         Usave = (double*)ctx_buffer(ctx, "md_Usave", (size_t)nP * 16);
         Uc = (double*)ctx_buffer(ctx, "U", 0);
-    }
-    bool nested() const { return p.n_inner > 0; }
-    // force of one level into out: outer = fermion (+ gauge on one level), inner = gauge
-    void force(bool outer, double* out) {
-        if (outer && phi) {
-            eofa_solve_info info[2];
-            int rc = eofa_force_dev(ctx, p.Ls, p.alpha, p.M5, p.m1, p.m2, p.precision, p.tol, phi, out, nullptr, info,
-                                    st);
-            if (rc != EOFA_OK) throw eofa_error(rc, "force evaluation failed in the trajectory: " + ctx->err);
-            nferm++;
-            iters += info[0].iters + info[1].iters;
-            if (!nested() && p.beta != 0.0) {
-                gauge_force_launch(ctx, Uc, p.beta, 1, out, st);
-                ngauge++;
+        if (!phi) {
+            kind = {F_GAUGE};
+            nsub = {p.nsteps};
+        } else if (p.split_lr) {
+            kind = {F_EOFA_R, F_EOFA_L};
+            nsub = {p.nsteps, p.n_middle};
+            if (p.beta != 0.0) {
+                kind.push_back(F_GAUGE);
+                nsub.push_back(p.n_inner);
             }
+        } else if (p.n_inner > 0) {
+            kind = {F_EOFA, F_GAUGE};
+            nsub = {p.nsteps, p.n_inner};
         } else {
+            kind = {p.beta != 0.0 ? F_EOFA_AND_GAUGE : F_EOFA};
+            nsub = {p.nsteps};
+        }
+    }
+    void force(int level, double* out) {
+        const Force k = kind[level];
+        if (k == F_GAUGE) {
             gauge_force_launch(ctx, Uc, p.beta, 0, out, st);
+            ngauge++;
+            return;
+        }
+        eofa_solve_info info[2];
+        int rc;
+        if (k == F_EOFA_L || k == F_EOFA_R)
+            rc = eofa_force_parts_dev(ctx, p.Ls, p.alpha, p.M5, p.m1, p.m2, p.precision, p.tol, phi,
+                                      k == F_EOFA_L ? out : nullptr, k == F_EOFA_R ? out : nullptr, info, st);
+        else
+            rc = eofa_force_dev(ctx, p.Ls, p.alpha, p.M5, p.m1, p.m2, p.precision, p.tol, phi, out, nullptr, info,
+                                st);
+        if (rc != EOFA_OK) throw eofa_error(rc, "force evaluation failed in the trajectory: " + ctx->err);
+        nferm++;
+        iters += info[0].iters + info[1].iters;
+        if (k == F_EOFA_AND_GAUGE) {
+            gauge_force_launch(ctx, Uc, p.beta, 1, out, st);
             ngauge++;
         }
     }
@@ -135,44 +165,45 @@ struct Trajectory {
         if (rc != EOFA_OK) throw eofa_error(rc, ctx->err);
     }
     // P <- P - c F(U'), U' = exp(-i z F(U)) U
-    void kick(bool outer, double c, double z) {
+    void kick(int level, double c, double z) {
         if (z != 0.0) {
-            force(outer, Fz);
+            force(level, Fz);
             EOFA_CUDA(cudaMemcpyAsync(Usave, Uc, (size_t)nP * 16, cudaMemcpyDeviceToDevice, st));
             links(-z, Fz);
-            force(outer, F);
+            force(level, F);
             EOFA_CUDA(cudaMemcpyAsync(Uc, Usave, (size_t)nP * 16, cudaMemcpyDeviceToDevice, st));
             launch_gauge_pack(ctx, Uc, st);
         } else {
-            force(outer, F);
+            force(level, F);
         }
         mom_update_kernel<<<nblk(nP, 256), 256, 0, st>>>(nP, c, (const double2*)F, (double2*)P);
         EOFA_LAUNCHED();
     }
-    void drift(bool outer, double t) {
-        if (outer && nested()) steps(false, t, p.n_inner);
+    void drift(int level, double t) {
+        if (level + 1 < (int)kind.size()) steps(level + 1, t);
         else links(t, P);
     }
-    void steps(bool outer, double t, int n) {
+    void steps(int level, double t) {
+        const int n = nsub[level];
         const double h = t / n;
         for (int k = 0; k < n; k++) {
             if (p.integrator == EOFA_INT_FG_PQPQP) {
-                kick(outer, h / 6, 0.0);
-                drift(outer, h / 2);
-                kick(outer, 2 * h / 3, h * h / 24);
-                drift(outer, h / 2);
-                kick(outer, h / 6, 0.0);
+                kick(level, h / 6, 0.0);
+                drift(level, h / 2);
+                kick(level, 2 * h / 3, h * h / 24);
+                drift(level, h / 2);
+                kick(level, h / 6, 0.0);
             } else if (p.integrator == EOFA_INT_FG_QPQPQ) {
                 const double lam = 0.5 - std::sqrt(3.0) / 6.0, z = (2.0 - std::sqrt(3.0)) / 12.0 * h * h;
-                drift(outer, lam * h);
-                kick(outer, h / 2, z);
-                drift(outer, (1 - 2 * lam) * h);
-                kick(outer, h / 2, z);
-                drift(outer, lam * h);
+                drift(level, lam * h);
+                kick(level, h / 2, z);
+                drift(level, (1 - 2 * lam) * h);
+                kick(level, h / 2, z);
+                drift(level, lam * h);
             } else {
-                kick(outer, h / 2, 0.0);
-                drift(outer, h);
-                kick(outer, h / 2, 0.0);
+                kick(level, h / 2, 0.0);
+                drift(level, h);
+                kick(level, h / 2, 0.0);
             }
         }
     }
@@ -193,9 +224,10 @@ struct Trajectory {
 extern "C" int eofa_hmc_trajectory_dev(eofa_ctx* ctx, const eofa_md_params* p, const double* phi_dev, double* P_dev,
                                        double* U_dev, eofa_md_info* info, void* stream) {
     if (!ctx || !p || !P_dev || !info) return fail(ctx, EOFA_EINVAL, "null argument");
+    const bool bad_split = p->split_lr && (!phi_dev || p->n_middle < 1 || (p->beta != 0.0 && p->n_inner < 1));
     if (p->nsteps < 1 || !(p->tau > 0) || p->n_inner < 0 || p->integrator < EOFA_INT_LEAPFROG ||
-        p->integrator > EOFA_INT_FG_QPQPQ || (p->n_inner > 0 && (!phi_dev || p->beta == 0.0)) ||
-        (!phi_dev && p->beta == 0.0))
+        p->integrator > EOFA_INT_FG_QPQPQ || (!p->split_lr && p->n_inner > 0 && (!phi_dev || p->beta == 0.0)) ||
+        (!phi_dev && p->beta == 0.0) || bad_split)
         return fail(ctx, EOFA_EINVAL, "bad trajectory parameters");
     cudaStream_t st = (cudaStream_t)stream;
     try {
@@ -203,7 +235,7 @@ extern "C" int eofa_hmc_trajectory_dev(eofa_ctx* ctx, const eofa_md_params* p, c
         Trajectory T(ctx, *p, phi_dev, P_dev, st);
         eofa_md_info r{};
         T.energy(&r.kinetic0, &r.S_gauge0, &r.S_eofa0);
-        T.steps(true, p->tau, p->nsteps);
+        T.steps(0, p->tau);
         T.energy(&r.kinetic1, &r.S_gauge1, &r.S_eofa1);
         r.H0 = r.kinetic0 + r.S_gauge0 + r.S_eofa0;
         r.dH = (r.kinetic1 + r.S_gauge1 + r.S_eofa1) - r.H0;

@@ -32,7 +32,7 @@ EXPORTS = [
     "eofa_solve_batched", "eofa_kernel_launches", "eofa_profile_start", "eofa_profile_stop",
     "eofa_dwf_apply_noalloc", "eofa_schur_hop_dev", "eofa_pseudofermion_solutions_dev",
     "eofa_set_reliable_delta", "eofa_leapfrog_dev", "eofa_rational_inv_sqrt", "eofa_heatbath_dev",
-    "eofa_gauge_action_dev", "eofa_gauge_force_dev", "eofa_hmc_trajectory_dev",
+    "eofa_gauge_action_dev", "eofa_gauge_force_dev", "eofa_hmc_trajectory_dev", "eofa_force_parts_dev",
 ]
 INT_LEAPFROG, INT_FG_PQPQP, INT_FG_QPQPQ = 0, 1, 2
 
@@ -59,7 +59,8 @@ class MDParams(ctypes.Structure):
     _fields_ = [("Ls", ctypes.c_int), ("alpha", ctypes.c_double), ("M5", ctypes.c_double), ("m1", ctypes.c_double),
                 ("m2", ctypes.c_double), ("precision", ctypes.c_int), ("tol", ctypes.c_double),
                 ("beta", ctypes.c_double), ("integrator", ctypes.c_int), ("nsteps", ctypes.c_int),
-                ("tau", ctypes.c_double), ("n_inner", ctypes.c_int)]
+                ("tau", ctypes.c_double), ("n_inner", ctypes.c_int), ("split_lr", ctypes.c_int),
+                ("n_middle", ctypes.c_int)]
 
 
 class MDInfo(ctypes.Structure):
@@ -125,6 +126,7 @@ def load_library(path: str = LIB_PATH):
                                                  ctypes.POINTER(SolveInfo), P]),
         "eofa_set_reliable_delta": (I, [P, D]),
         "eofa_gauge_action_dev": (I, [P, D, P, ctypes.POINTER(D), P]),
+        "eofa_force_parts_dev": (I, [P, I, D, D, D, D, I, D, P, P, P, ctypes.POINTER(SolveInfo), P]),
         "eofa_gauge_force_dev": (I, [P, D, P, P, I, P]),
         "eofa_hmc_trajectory_dev": (I, [P, ctypes.POINTER(MDParams), P, P, P, ctypes.POINTER(MDInfo), P]),
         "eofa_rational_inv_sqrt": (I, [I, D, D, ctypes.POINTER(D), P, P, ctypes.POINTER(D)]),
@@ -400,6 +402,15 @@ class Lattice:
         self._check(rc, "leapfrog_dev")
         return dH.value, H0.value
 
+    def force_parts_dev(self, phi, FL, FR, alpha, M5, m1, m2, precision=PREC_F64, tol=1e-10):
+        """Forces of S_L and S_R separately (either output may be None); returns the two solve records."""
+        info = (SolveInfo * 2)()
+        rc = self.lib.eofa_force_parts_dev(self.ctx, self.Ls, alpha, M5, m1, m2, precision, tol, _ptr(phi),
+                                           _ptr(FL) if FL is not None else None, _ptr(FR) if FR is not None else None,
+                                           info, _stream())
+        self._check(rc, "force_parts_dev")
+        return [info[0].as_dict(), info[1].as_dict()]
+
     def gauge_action_dev(self, beta, U=None):
         """Wilson plaquette action of U (device canonical) or of the context's links."""
         S = ctypes.c_double()
@@ -412,9 +423,11 @@ class Lattice:
                                                   int(accumulate), _stream()), "gauge_force_dev")
 
     def hmc_trajectory_dev(self, P, phi=None, U=None, *, alpha=2.0, M5=1.8, m1=0.04, m2=1.0, precision=PREC_F64,
-                           tol=1e-10, beta=0.0, integrator=INT_FG_QPQPQ, nsteps=4, tau=1.0, n_inner=0):
+                           tol=1e-10, beta=0.0, integrator=INT_FG_QPQPQ, nsteps=4, tau=1.0, n_inner=0,
+                           split_lr=False, n_middle=0):
         """One MD trajectory (P and the context's links updated in place); returns the info dict."""
-        prm = MDParams(self.Ls, alpha, M5, m1, m2, precision, tol, beta, integrator, nsteps, tau, n_inner)
+        prm = MDParams(self.Ls, alpha, M5, m1, m2, precision, tol, beta, integrator, nsteps, tau, n_inner,
+                       int(split_lr), n_middle)
         info = MDInfo()
         rc = self.lib.eofa_hmc_trajectory_dev(self.ctx, ctypes.byref(prm), _ptr(phi) if phi is not None else None,
                                               _ptr(P), _ptr(U) if U is not None else None, ctypes.byref(info),

@@ -123,3 +123,53 @@ def test_trajectory_rejects_bad_parameters(eofa):
     with pytest.raises(eofa.EOFAError):
         lat.hmc_trajectory_dev(Pd, None, None, beta=BETA, n_inner=2)  # nesting needs a fermion level
     lat.close()
+
+
+def test_force_parts_match_oracle(eofa):
+    """Eq. (7) term by term on the device: F_L + F_R = F, each part vs the oracle."""
+    import torch
+    from oracle import eofa as oeofa
+    dims, Ls = (4, 4, 2, 4), 6
+    U = inputs.gauge_field(dims, 0.5, 21)
+    phi = inputs.fermion4d(dims, 22)
+    lat = eofa.Lattice(dims, Ls)
+    lat.gauge_load(U)
+    shape = U.shape
+    FL = torch.empty(shape, dtype=torch.complex128, device="cuda")
+    FR = torch.empty_like(FL)
+    info = lat.force_parts_dev(_dev(phi), FL, FR, ALPHA, M5, M1, M2, tol=1e-13)
+    assert info[0]["iters"] > 0 and info[1]["iters"] > 0
+    F, _, _ = lat.force(phi, ALPHA, M5, M1, M2, precision=0, tol=1e-13)
+    fl, fr = FL.cpu().numpy(), FR.cpu().numpy()
+    assert np.abs(fl + fr - F).max() < 1e-9 * np.abs(F).max()
+    for part, got in (("L", fl), ("R", fr)):
+        ref = oeofa.force_part(U, phi, Ls, ALPHA, M5, M1, M2, -1.0, part, tol=1e-13)
+        assert np.abs(got - ref).max() < 1e-9 * np.abs(ref).max(), part
+    only = torch.zeros_like(FL)
+    info = lat.force_parts_dev(_dev(phi), None, only, ALPHA, M5, M1, M2, tol=1e-13)
+    assert info[0]["iters"] == 0 and np.abs(only.cpu().numpy() - fr).max() < 1e-9 * np.abs(fr).max()
+    lat.close()
+
+
+def test_split_lr_trajectory_matches_oracle(eofa):
+    """Asymmetric integration: S_R force outermost, S_L force in the middle, gauge innermost."""
+    import torch
+    dims, Ls = (2, 2, 2, 2), 4
+    U = inputs.gauge_field(dims, 0.4, 23)
+    P = inputs.momenta(dims, 24)
+    phi = inputs.fermion4d(dims, 25)
+    lat = eofa.Lattice(dims, Ls)
+    lat.gauge_load(U)
+    Pd = _dev(P)
+    Ud = torch.empty_like(Pd)
+    info = lat.hmc_trajectory_dev(Pd, _dev(phi), Ud, alpha=ALPHA, M5=M5, m1=M1, m2=M2, tol=1e-13, beta=BETA,
+                                  integrator=eofa.INT_FG_QPQPQ, nsteps=1, tau=0.4, n_inner=1, split_lr=True,
+                                  n_middle=2)
+    ferm = dict(phi=phi, Ls=Ls, alpha=ALPHA, M5=M5, m1=M1, m2=M2, bc_t=-1.0, tol=1e-13)
+    U1, P1, dH = gauge.split_lr_trajectory(U, P, BETA, ferm, 0.4, 1, 2, 1, "qpqpq")
+    # 4 S_R forces (two displaced kicks) + 3 drifts x 2 steps x 4 S_L forces
+    assert info["fermion_forces"] == 28
+    assert np.abs(Ud.cpu().numpy() - U1).max() < 1e-10
+    assert np.abs(Pd.cpu().numpy() - P1).max() < 1e-9
+    assert info["dH"] == pytest.approx(dH, abs=1e-8)
+    lat.close()

@@ -196,3 +196,27 @@ def test_heatbath_eq6_equals_dense_rational_function(U):
     exact = (vec @ (f * (vec.conj().T @ eta.reshape(-1)))).reshape(eta.shape)
     phi = oeofa.heatbath(U, eta, LS, ALPHA, M5, M1, M2, BC, a0, al, be, tol=1e-13)
     assert np.linalg.norm(phi - exact) < 1e-10 * np.linalg.norm(exact)
+
+
+def test_force_parts_match_partial_action_differences(U):
+    """Eq. (7) term by term: the chi_L part of the force is the derivative of
+    S_L = phi_-^+ M_L phi_-, the chi_R part that of S_R; S_L + S_R = S."""
+    phi = inputs.fermion4d(DIMS, 5)
+    args = (LS, ALPHA, M5, M1, M2, BC)
+    SL, SR = oeofa.partial_actions(U, phi, *args, tol=1e-13)
+    assert SL + SR == pytest.approx(oeofa.action(U, phi, *args, tol=1e-13), rel=1e-11)
+    T = oeofa.generators()
+    rng = np.random.default_rng(4)
+    d = 1e-4
+    for part, idx in (("L", 0), ("R", 1)):
+        Fa = oeofa.force_components(oeofa.force_part(U, phi, *args, part, tol=1e-13))
+        for _ in range(2):
+            site = tuple(int(rng.integers(n)) for n in U.shape[:4])
+            mu, a = int(rng.integers(4)), int(rng.integers(8))
+            vals = []
+            for w in (d, -d):
+                Up = U.copy()
+                Up[site + (mu,)] = oeofa.exp_i(w * T[a]) @ U[site + (mu,)]
+                vals.append(oeofa.partial_actions(Up, phi, *args, tol=1e-13)[idx])
+            fd = (vals[0] - vals[1]) / (2 * d)
+            assert abs(fd - Fa[site + (mu, a)]) < 1e-6 * max(1.0, abs(fd)), (part, fd, Fa[site + (mu, a)])
