@@ -199,6 +199,79 @@ def hop_only(args, wl):
     return 0
 
 
+MD_WORKLOAD = dict(dims=(16, 16, 16, 32), Ls=12, eps=0.5, seed=4, alpha=2.0, M5=1.8, m1=0.04, m2=1.0, bc=-1)
+
+
+def heatbath_bench(args):
+    """phi = f(M_EOFA) eta, 12-pole Zolotarev f ~ x^-1/2 on [1e-3, 20], mixed F32 solves to 1e-10."""
+    import torch
+
+    from paper_1611_00298_gb300 import build, eofa, inputs
+    if not os.path.exists(eofa.LIB_PATH):
+        build.build()
+    w = MD_WORKLOAD
+    lat = eofa.Lattice(w["dims"], w["Ls"], bc_t=w["bc"])
+    lat.gauge_load(inputs.gauge_field(w["dims"], w["eps"], w["seed"]))
+    eta = torch.from_numpy(inputs.fermion4d(w["dims"], 9)).cuda()
+    phi = torch.empty_like(eta)
+    a0, al, be, err = eofa.rational_inv_sqrt(12, 1e-3, 20.0)
+    out = {"heatbath": True, "lattice": "x".join(map(str, w["dims"])), "Ls": w["Ls"], "poles": 12,
+           "interval": [1e-3, 20.0], "rational_max_rel_err": err}
+    for forecast in (False, True):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        info = lat.heatbath_dev(eta, phi, w["alpha"], w["M5"], w["m1"], w["m2"], a0, al, be,
+                                precision=eofa.PREC_MIXED_F32, tol=1e-10, forecast=forecast)
+        torch.cuda.synchronize()
+        key = "forecast" if forecast else "zero_guess"
+        out[key] = {"seconds": round(time.perf_counter() - t0, 3), "iters": sum(i.iters for i in info),
+                    "iters_per_solve": [i.iters for i in info]}
+    out["iteration_ratio"] = round(out["forecast"]["iters"] / out["zero_guess"]["iters"], 3)
+    print(json.dumps(out), flush=True)
+    lat.close()
+    return 0
+
+
+def hmc_bench(args):
+    """One trajectory (tau = 1) of H = tr P^2 + S_g(beta 5.7) + S_EOFA, nested QPQPQ, mixed F32 solves."""
+    import torch
+
+    from paper_1611_00298_gb300 import build, eofa, inputs
+    if not os.path.exists(eofa.LIB_PATH):
+        build.build()
+    w = MD_WORKLOAD
+    U = inputs.gauge_field(w["dims"], w["eps"], w["seed"])
+    P0 = inputs.momenta(w["dims"], 5)
+    phi = torch.from_numpy(inputs.fermion4d(w["dims"], 6)).cuda()
+    lat = eofa.Lattice(w["dims"], w["Ls"], bc_t=w["bc"])
+    out = {"hmc": True, "lattice": "x".join(map(str, w["dims"])), "Ls": w["Ls"], "beta": 5.7, "tau": 1.0,
+           "integrator": "force-gradient QPQPQ"}
+    kw = dict(alpha=w["alpha"], M5=w["M5"], m1=w["m1"], m2=w["m2"], precision=eofa.PREC_MIXED_F32, tol=1e-10,
+              beta=5.7, integrator=eofa.INT_FG_QPQPQ, tau=1.0)
+    lat.gauge_load(U)
+    FL = torch.empty(U.shape, dtype=torch.complex128, device="cuda")
+    FR = torch.empty_like(FL)
+    lat.force_parts_dev(phi, FL, FR, w["alpha"], w["M5"], w["m1"], w["m2"], precision=eofa.PREC_MIXED_F32, tol=1e-10)
+    # size of the two EOFA force terms (the L / R asymmetry behind split integration)
+    rms = lambda F: float(torch.sqrt((F.abs() ** 2).sum(dim=(-1, -2)).mean()))  # noqa: E731
+    out["force_rms"] = {"L": rms(FL), "R": rms(FR)}
+    out["force_max"] = {"L": float(FL.abs().amax()), "R": float(FR.abs().amax())}
+    for name, extra in (("nested", dict(nsteps=4, n_inner=2)),
+                        ("split_lr", dict(nsteps=2, n_middle=2, n_inner=2, split_lr=True))):
+        lat.gauge_load(U)
+        P = torch.from_numpy(P0).cuda()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        info = lat.hmc_trajectory_dev(P, phi, None, **kw, **extra)
+        torch.cuda.synchronize()
+        out[name] = dict(extra, seconds=round(time.perf_counter() - t0, 3), dH=info["dH"],
+                         fermion_forces=info["fermion_forces"], gauge_forces=info["gauge_forces"],
+                         solver_iters=info["solver_iters"])
+    print(json.dumps(out), flush=True)
+    lat.close()
+    return 0
+
+
 def batched(args):
     """Three lattices x (3 mass pairs x {L, R} EOFA systems + 2 D_DWF systems) = 24 solves."""
     import numpy as np
@@ -281,6 +354,12 @@ def main():
     ap.add_argument("--hop-reps", type=int, default=4)
     ap.add_argument("--schur", action="store_true", help="with --hop-only: the fused G^-1 D_hop kernel")
     ap.add_argument("--hop-precision", default=None, choices=["f64", "f32", "f16"])
+    ap.add_argument("--heatbath", action="store_true",
+                    help="EOFA heatbath (Eq. (6)) at 16^3x32, Ls=12: solver iterations and time with and without "
+                         "chronological initial guesses")
+    ap.add_argument("--hmc", action="store_true",
+                    help="one nested force-gradient QPQPQ trajectory at 16^3x32, Ls=12 (EOFA + Wilson gauge), "
+                         "one level and split L/R")
     ap.add_argument("--batched", action="store_true",
                     help="24 solves on three lattices (8^4x8, 12^4x12, 16^3x32x16): one batched, graph-captured "
                          "mixed-precision call vs sequential FP64 solves")
@@ -292,6 +371,10 @@ def main():
         return hop_only(args, wl)
     if args.batched:
         return batched(args)
+    if args.heatbath:
+        return heatbath_bench(args)
+    if args.hmc:
+        return hmc_bench(args)
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -353,11 +436,12 @@ def main():
     barrier()
     elapsed = ev0.elapsed_time(ev1) / 1000.0
     launches = eofa.kernel_launches() - l0
-    hop_launches, kind_ms = lat.profile_stop()
+    hop_launches, kind_ms, kind_bytes = lat.profile_stop()
     clk = clocks.stop()
 
-    bytes_per_hop = [hop_bytes_per_site(p, Ls) * n5h for p in range(3)]
-    hop_bytes = sum(hop_launches[p] * bytes_per_hop[p] for p in range(3))
+    # algorithmic bytes counted per launch by the library (each spinor read /
+    # written once, links once per 4D site, the axpy input when present)
+    hop_bytes = sum(kind_bytes[p] for p in range(3))
     t_max = elapsed
     total_bytes = hop_bytes
     if dist is not None:
@@ -371,14 +455,15 @@ def main():
 
     inner = 1 if prec == eofa.PREC_MIXED_F32 else 2
     avg_ms = kind_ms[inner] / max(1, hop_launches[inner])
-    achieved = bytes_per_hop[inner] / (avg_ms / 1000.0) / 1e9
+    avg_bytes = kind_bytes[inner] / max(1, hop_launches[inner])
+    achieved = avg_bytes / (avg_ms / 1000.0) / 1e9
     peak, peak_src = hbm_peak()
     traffic = None
     tpath = os.path.join(ROOT, "profiles", "hop_traffic.json")
     if os.path.exists(tpath):
         try:
             td = json.load(open(tpath))
-            key = f"{'fp32' if inner == 1 else 'fp16'}_24x24x24x64_Ls24"
+            key = f"{'fp32' if inner == 1 else 'fp16'}_solver_24x24x24x64_Ls24"
             if key in td and td[key].get("kernel_version") == kernel_version():
                 traffic = td[key]["bytes_per_launch"]
         except Exception:
@@ -397,8 +482,8 @@ def main():
                       tol=1e-10, out=F_h.numpy())
         torch.cuda.synchronize()
         e2e_t = (time.perf_counter() - t0) / args.steps
-        hl2, _ = lat.profile_stop()
-        e2e_bytes = sum(hl2[p] * bytes_per_hop[p] for p in range(3)) / args.steps
+        _, _, b2 = lat.profile_stop()
+        e2e_bytes = sum(b2[p] for p in range(3)) / args.steps
         e2e = {"value": round(e2e_bytes / e2e_t / 1e9, 2), "unit": "GB/s",
                "h2d_bytes_per_step": int(phi_np.nbytes), "d2h_bytes_per_step": int(F_h.numel() * 16 + 8),
                "seconds_per_step": round(e2e_t, 4)}
@@ -424,8 +509,9 @@ def main():
         hop_share = kind_ms[inner] / 1000.0 / elapsed
         roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                     "frac": round(achieved / peak, 4), "traffic": traffic,
-                    "kernel": f"even-odd hop, {'FP32' if inner == 1 else 'FP16'} storage, all Ls slices",
-                    "bytes_per_launch": int(bytes_per_hop[inner]), "avg_launch_ms": round(avg_ms, 4),
+                    "kernel": f"fused even-odd dslash (hop + 5D-local + axpy), {'FP32' if inner == 1 else 'FP16'} "
+                              "storage, all Ls slices",
+                    "bytes_per_launch": int(avg_bytes), "avg_launch_ms": round(avg_ms, 4),
                     "launches_timed": hop_launches[inner], "share_of_step": round(hop_share, 4),
                     "peak_source": f"{peak_src} ({'of measured' if peak_src == 'measured' else 'of fallback'})"}
         result = {

@@ -325,11 +325,16 @@ int eofa_dwf_apply_noalloc(eofa_ctx* ctx, int Ls, double alpha, double M5, doubl
  * eofa_profile_start / _stop: while on, every even-odd hop and 5D-local
  * kernel launch on the context is bracketed by CUDA events recorded on its
  * stream (at most 65536 launches); _stop waits for them and returns per-kind
- * launch counts and summed milliseconds.  Kinds: 0..2 hop in
- * FP64 / FP32 / FP16 storage, 3..5 5D-local kernel in the same order. */
+ * launch counts, summed milliseconds and summed algorithmic bytes (each
+ * spinor read or written once per launch, 8 links per 4D output site read
+ * once: per output site 2 spinors + 576/Ls (FP32 links) or 1152/Ls (FP64)
+ * bytes, plus one spinor for the axpy input y when present).  Kinds: 0..2
+ * hop in FP64 / FP32 / FP16 storage, 3..5 5D-local kernel in the same
+ * order. */
 typedef struct {
     long long launches[6];
     double ms[6];
+    double bytes[6];
 } eofa_profile;
 long long eofa_kernel_launches(void);
 int eofa_profile_start(eofa_ctx* ctx);

@@ -82,8 +82,9 @@ static void build_neighbours(eofa_ctx* ctx, std::vector<int>& nb) {
                                 if (d[mu] < 0) { d[mu] = n[mu] - 1; wrap = true; }
                             }
                             int in_ = d[0] + X * (d[1] + Y * (d[2] + Z * d[3]));
+                            // the t-boundary phase lives in the packed t-links at t = T - 1
+                            (void)wrap;
                             int e = in_ / 2;
-                            if (mu == 3 && wrap && ctx->bc_t < 0) e |= (int)0x80000000u;
                             nb[(size_t)par * 8 * Vh + (size_t)(2 * mu + dirn) * Vh + j] = e;
                         }
                 }
@@ -164,12 +165,15 @@ int eofa_create(eofa_ctx** out, const int dims[4], int Ls, int bc_t, int flags) 
     ctx->tuned = new std::map<long long, int>();
     ctx->forced_cfg = 0;
     if (const char* env = getenv("EOFA_DSLASH_CONFIG")) {
-        // "NS,SPT" selects the direct kernel, "NS,SPT,D" the staged one with ring depth D
+        // "NS,SPT" selects the direct kernel, "NS,SPT,D" the staged one with ring
+        // depth D, "NS,SPT,-K" the pipelined one with K slots per thread
         int ns = 0, spt = 0, depth = 0;
         const int n = sscanf(env, "%d,%d,%d", &ns, &spt, &depth);
-        if (n >= 2 && ns >= 1 && ns <= 64 && (spt == 1 || spt == 2))
-            ctx->forced_cfg = (n == 3 && depth >= 2 && depth <= 8 && ns <= 32) ? ((1 << 20) | depth << 8 | ns)
-                                                                                : ns * 4 + spt;
+        if (n >= 2 && ns >= 1 && ns <= 64 && (spt == 1 || spt == 2)) {
+            ctx->forced_cfg = ns * 4 + spt;
+            if (n == 3 && depth >= 2 && depth <= 8 && ns <= 32) ctx->forced_cfg = (1 << 20) | depth << 8 | ns;
+            if (n == 3 && depth <= -2 && depth >= -3) ctx->forced_cfg = (1 << 21) | (-depth) << 8 | ns;
+        }
     }
     ctx->rel_delta = 0.0;  // precision default
     try {

@@ -16,10 +16,15 @@ Op5 op_identity() {
     return op;
 }
 
+// bytes of one spinor (site, slice) as stored, per precision (FP16 with its scale)
+static double spinor_bytes(int prec) { return prec == P64 ? 192.0 : prec == P32 ? 96.0 : 52.0; }
+
 void fused_dslash(const eofa_ctx* ctx, int prec, int out_parity, int dagger, const void* in, void* out, const Op5& op,
                   const void* y, double a_out, double b_in, double* red, int slot, cudaStream_t st) {
     const Op5 opf = op_finalize(op, ctx->Ls);
-    prof_begin(ctx, prec, st);
+    const double n5h = (double)ctx->Vh * ctx->Ls;
+    const double bytes = n5h * spinor_bytes(prec) * (y ? 3.0 : 2.0) + 8.0 * ctx->Vh * (prec == P64 ? 144.0 : 72.0);
+    prof_begin(ctx, prec, st, bytes);
     if (prec == P64) dslash_p64(ctx, out_parity, dagger, in, out, opf, y, a_out, b_in, red, slot, st);
     else if (prec == P32) dslash_p32(ctx, out_parity, dagger, in, out, opf, y, a_out, b_in, red, slot, st);
     else dslash_p16(ctx, out_parity, dagger, in, out, opf, y, a_out, b_in, red, slot, st);
@@ -30,7 +35,8 @@ void fused_local5(const eofa_ctx* ctx, int prec, const Op5& op, const void* x, c
                   const double* sc, int it, int use_alpha, void* xw, void* out, double a_out, double* red, int slot,
                   cudaStream_t st) {
     const Op5 opf = op_finalize(op, ctx->Ls);
-    prof_begin(ctx, 3 + prec, st);
+    const double nf = 1.0 + (z ? 1.0 : 0.0) + (xw ? 1.0 : 0.0) + (out ? 1.0 : 0.0);
+    prof_begin(ctx, 3 + prec, st, (double)ctx->Vh * ctx->Ls * spinor_bytes(prec) * nf);
     if (prec == P64) local5_p64(ctx, opf, x, z, c0, sc, it, use_alpha, xw, out, a_out, red, slot, st);
     else if (prec == P32) local5_p32(ctx, opf, x, z, c0, sc, it, use_alpha, xw, out, a_out, red, slot, st);
     else local5_p16(ctx, opf, x, z, c0, sc, it, use_alpha, xw, out, a_out, red, slot, st);

@@ -87,14 +87,15 @@ __device__ __forceinline__ void consumer_sync(int nthreads) {
     asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
 }
 
-// Row geometry of one 4D site in shared memory: the spinor row as stored in
-// HBM (RB bytes per slice) followed, in FP16, by the per-slice scales.
+// Row geometry of one 4D site: the spinor row as stored in HBM (RB bytes per
+// slice) and, in FP16, the row of per-slice scales (SB bytes per slice).
 template <int P>
 struct SRow;
 template <>
 struct SRow<P64> {
     static constexpr int RB = 192, SB = 0, LB = 144;
-    static __device__ __forceinline__ void load(const unsigned char* row, int s, int Ls, cpx<double> v[12]) {
+    static __device__ __forceinline__ void load(const unsigned char* row, const float*, int s, int Ls,
+                                                cpx<double> v[12]) {
         const double2* b = reinterpret_cast<const double2*>(row) + s;
 #pragma unroll
         for (int c = 0; c < 12; c++) {
@@ -106,7 +107,8 @@ struct SRow<P64> {
 template <>
 struct SRow<P32> {
     static constexpr int RB = 96, SB = 0, LB = 80;
-    static __device__ __forceinline__ void load(const unsigned char* row, int s, int Ls, cpx<float> v[12]) {
+    static __device__ __forceinline__ void load(const unsigned char* row, const float*, int s, int Ls,
+                                                cpx<float> v[12]) {
         const float4* b = reinterpret_cast<const float4*>(row) + s;
 #pragma unroll
         for (int k = 0; k < 6; k++) {
@@ -119,9 +121,10 @@ struct SRow<P32> {
 template <>
 struct SRow<P16> {
     static constexpr int RB = 48, SB = 4, LB = 80;
-    static __device__ __forceinline__ void load(const unsigned char* row, int s, int Ls, cpx<float> v[12]) {
+    static __device__ __forceinline__ void load(const unsigned char* row, const float* scale, int s, int Ls,
+                                                cpx<float> v[12]) {
         const uint4* b = reinterpret_cast<const uint4*>(row) + s;
-        const float sc = reinterpret_cast<const float*>(row + 48 * Ls)[s];
+        const float sc = scale[s];
 #pragma unroll
         for (int k = 0; k < 3; k++) {
             const uint4 t = b[k * Ls];
@@ -136,37 +139,41 @@ struct SRow<P16> {
     }
 };
 
-// Shared-memory plan of one block (host and device agree on it).
+// Shared-memory plan of one block (host and device agree on it).  A ring
+// slot holds NS spinor rows, then NS scale rows (FP16), then NS links, each
+// group contiguous so that neighbours with consecutive indices arrive in one
+// copy.
 struct BulkPlan {
-    int site_b, stage_b, col_b, ring_b, total_b;
+    int row_b, sc_off, lk_off, stage_b, col_b, ring_b, total_b;
 };
 
 template <int P, typename R>
 __host__ __device__ __forceinline__ BulkPlan bulk_plan(int NS, int D, int Ls, bool hasop) {
     BulkPlan b;
-    b.site_b = (SRow<P>::RB + SRow<P>::SB) * Ls;
-    b.stage_b = (NS * (b.site_b + SRow<P>::LB) + 127) / 128 * 128;
+    b.row_b = SRow<P>::RB * Ls;
+    b.sc_off = NS * b.row_b;
+    b.lk_off = b.sc_off + NS * SRow<P>::SB * Ls;
+    b.stage_b = (b.lk_off + NS * SRow<P>::LB + 127) / 128 * 128;
     b.ring_b = D * b.stage_b;
     b.col_b = hasop ? (NS * 12 * (Ls + 1) * (int)sizeof(cpx<R>) + 127) / 128 * 128 : 0;
-    // + full[D], empty[D] (8 bytes each), sign[D], abort flag
-    b.total_b = b.ring_b + b.col_b + 16 * D + 4 * D + 16;
+    // + full[D], empty[D] (8 bytes each), abort flag
+    b.total_b = b.ring_b + b.col_b + 16 * D + 16;
     return b;
 }
 
 // One hop direction from a staged ring slot: neighbour spinor from the row
 // of site ls, link from the slot's link records (row of U, or of U^+).
 template <int P, int DAG, int MU, int DIRN, typename R>
-__device__ __forceinline__ void staged_dir(const unsigned char* stage, int site_b, int NS, unsigned signs, int ls, int s,
-                                           int Ls, cpx<R>* acc) {
+__device__ __forceinline__ void staged_dir(const unsigned char* stage, const BulkPlan& pl, int ls, int s, int Ls,
+                                           cpx<R>* acc) {
     cpx<R> h[6];
     {
         cpx<R> psi[12];
-        SRow<P>::load(stage + ls * site_b, s, Ls, psi);
-        const bool neg = (signs >> ls) & 1u;
-        if (DIRN == 0) project<MU, DAG ? 1 : -1>(psi, neg, h);
-        else project<MU, DAG ? -1 : 1>(psi, neg, h);
+        SRow<P>::load(stage + ls * pl.row_b, reinterpret_cast<const float*>(stage + pl.sc_off) + ls * Ls, s, Ls, psi);
+        if (DIRN == 0) project<MU, DAG ? 1 : -1>(psi, h);
+        else project<MU, DAG ? -1 : 1>(psi, h);
     }
-    const cpx<R>* lk = reinterpret_cast<const cpx<R>*>(stage + NS * site_b + ls * SRow<P>::LB);
+    const cpx<R>* lk = reinterpret_cast<const cpx<R>*>(stage + pl.lk_off + ls * SRow<P>::LB);
 #pragma unroll
     for (int a = 0; a < 3; a++) {
         cpx<R> u[3];
@@ -203,8 +210,7 @@ __global__ void __launch_bounds__(BULK_MAX_THREADS, 2) dslash_bulk_kernel(
     cpx<R>* col = reinterpret_cast<cpx<R>*>(smraw + pl.ring_b);
     unsigned long long* full = reinterpret_cast<unsigned long long*>(smraw + pl.ring_b + pl.col_b);
     unsigned long long* empty = full + D;
-    unsigned* signs = reinterpret_cast<unsigned*>(empty + D);
-    volatile int* abort_flag = reinterpret_cast<volatile int*>(signs + D);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + D);
     const int NC = (NS * Ls + 31) / 32 * 32;  // consumer threads
     const int nd = y != nullptr ? 9 : 8;      // stages per tile
     const long long n5 = (long long)g.Vh * Ls;
@@ -259,27 +265,31 @@ __global__ void __launch_bounds__(BULK_MAX_THREADS, 2) dslash_bulk_kernel(
                     unsigned char* stg = ring + rg.slot * pl.stage_b;
                     const unsigned fb = smem_addr(full + rg.slot);
                     const int ed = d < 8 ? e[d] : 0;
-                    const int jn = d < 8 ? (ed & 0x7fffffff) : j;
-                    const unsigned neg = __ballot_sync(0xffffffffu, act && d < 8 && ed < 0);
-                    const unsigned bytes = (unsigned)(nsites * (pl.site_b + (d < 8 ? SRow<P>::LB : 0)));
-                    if (lane == 0) {
-                        signs[rg.slot] = neg;
-                        mbar_arrive_tx(fb, bytes);
-                    }
+                    const int jn = d < 8 ? ed : j;
+                    const unsigned bytes =
+                        (unsigned)(nsites * ((SRow<P>::RB + SRow<P>::SB) * Ls + (d < 8 ? SRow<P>::LB : 0)));
+                    if (lane == 0) mbar_arrive_tx(fb, bytes);
                     __syncwarp();
-                    if (act) {
+                    // runs of consecutive neighbour indices travel in one copy each
+                    const int prev = __shfl_up_sync(0xffffffffu, jn, 1);
+                    const bool start = act && (lane == 0 || jn != prev + 1);
+                    const unsigned starts = __ballot_sync(0xffffffffu, start);
+                    if (start) {
+                        const unsigned later = starts & (0xfffffffeu << lane);
+                        const int len = (later ? __ffs(later) - 1 : nsites) - lane;
                         const unsigned char* base = d < 8 ? inb : yb;
-                        const unsigned dst = smem_addr(stg + lane * pl.site_b);
-                        bulk_g2s(dst, base + (size_t)jn * row_b, (unsigned)row_b, fb);
+                        bulk_g2s(smem_addr(stg + lane * pl.row_b), base + (size_t)jn * row_b,
+                                 (unsigned)(len * row_b), fb);
                         if (SRow<P>::SB)
-                            bulk_g2s(dst + (unsigned)row_b, base + n5 * SRow<P>::RB + (size_t)jn * SRow<P>::SB * Ls,
-                                     (unsigned)(SRow<P>::SB * Ls), fb);
+                            bulk_g2s(smem_addr(stg + pl.sc_off + lane * SRow<P>::SB * Ls),
+                                     base + n5 * SRow<P>::RB + (size_t)jn * SRow<P>::SB * Ls,
+                                     (unsigned)(len * SRow<P>::SB * Ls), fb);
                         if (d < 8) {
                             const int mu = d >> 1;
                             const long long lidx = (d & 1) == 0 ? (long long)(par * 4 + mu) * g.Vh + j
                                                                 : (long long)((1 - par) * 4 + mu) * g.Vh + jn;
-                            bulk_g2s(smem_addr(stg + NS * pl.site_b + lane * SRow<P>::LB),
-                                     gb + lidx * SRow<P>::LB, SRow<P>::LB, fb);
+                            bulk_g2s(smem_addr(stg + pl.lk_off + lane * SRow<P>::LB), gb + lidx * SRow<P>::LB,
+                                     (unsigned)(len * SRow<P>::LB), fb);
                         }
                     }
                     issued++;
@@ -319,8 +329,7 @@ __global__ void __launch_bounds__(BULK_MAX_THREADS, 2) dslash_bulk_kernel(
     {                                                                                                       \
         if (ok) ok = mbar_wait(smem_addr(full + rg.slot), rg.phase, abort_flag, err);                      \
         if (ok && site_ok)                                                                                  \
-            staged_dir<P, DAG, MU, DIRN, R>(ring + rg.slot * pl.stage_b, pl.site_b, NS, signs[rg.slot], ls, s, \
-                                            Ls, acc);                                                       \
+            staged_dir<P, DAG, MU, DIRN, R>(ring + rg.slot * pl.stage_b, pl, ls, s, Ls, acc);                 \
         __syncwarp();                                                                                       \
         if (lane == 0) mbar_arrive(smem_addr(empty + rg.slot));                                             \
         rg.next();                                                                                          \
@@ -348,7 +357,9 @@ __global__ void __launch_bounds__(BULK_MAX_THREADS, 2) dslash_bulk_kernel(
                 if (ok) ok = mbar_wait(smem_addr(full + rg.slot), rg.phase, abort_flag, err);
                 if (ok && site_ok) {
                     cpx<R> yv[12];
-                    SRow<P>::load(ring + rg.slot * pl.stage_b + ls * pl.site_b, s, Ls, yv);
+                    const unsigned char* stg = ring + rg.slot * pl.stage_b;
+                    SRow<P>::load(stg + ls * pl.row_b, reinterpret_cast<const float*>(stg + pl.sc_off) + ls * Ls, s,
+                                  Ls, yv);
                     const R bb = (R)b_in;
 #pragma unroll
                     for (int c = 0; c < 12; c++) acc[c] = acc[c] + bb * yv[c];

@@ -32,6 +32,10 @@
 #ifndef EOFA_HOP_MINB
 #define EOFA_HOP_MINB 3
 #endif
+// 1: load the eight neighbour entries of a site before its first spinor load
+#ifndef EOFA_HOP_PREFETCH
+#define EOFA_HOP_PREFETCH 1
+#endif
 
 namespace dsl {
 namespace {
@@ -75,21 +79,18 @@ __device__ __forceinline__ void link_row<float>(const void* g, long long idx, in
 }
 
 // (1 + SG gamma_mu) psi has upper half h = psi_u + SG A psi_l (two colour
-// vectors h0, h1) and lower half SG A^+ h.  project forms h (negated for a
-// boundary phase of -1); mac_row adds row a of V h (V = U or U^+, one link
-// row u) to the upper spins and, through A^+, to the lower spins.
+// vectors h0, h1) and lower half SG A^+ h.  project forms h; mac_row adds
+// row a of V h (V = U or U^+, one link row u) to the upper spins and,
+// through A^+, to the lower spins.  The time-boundary phase is carried by
+// the packed links.
 template <int MU, int SG, typename R>
-__device__ __forceinline__ void project(const cpx<R>* psi, bool neg, cpx<R>* h) {
+__device__ __forceinline__ void project(const cpx<R>* psi, cpx<R>* h) {
     cpx<R> a0[3], a1[3];
     apply_A<MU>(psi + 6, psi + 9, a0, a1);
 #pragma unroll
     for (int c = 0; c < 3; c++) {
         h[c] = SG > 0 ? psi[c] + a0[c] : psi[c] - a0[c];
         h[3 + c] = SG > 0 ? psi[3 + c] + a1[c] : psi[3 + c] - a1[c];
-        if (neg) {
-            h[c] = mk(-h[c].re, -h[c].im);
-            h[3 + c] = mk(-h[3 + c].re, -h[3 + c].im);
-        }
     }
 }
 
@@ -111,21 +112,22 @@ __device__ __forceinline__ void mac_row(const cpx<R>* u, int a, const cpx<R>* h,
 // One direction pair for SPT slices s[0..SPT) of site j: the neighbour index
 // and every link row are loaded once and used for all SPT slices.
 template <int P, int DAG, int MU, int SPT>
-__device__ __forceinline__ void hop_mu(const Geom& g, int par, int j, const int* sv, int Ls, long long n5,
-                                       const void* in, const void* gauge, cpx<typename Field<P>::R> (*acc)[12]) {
+__device__ __forceinline__ void hop_mu(const Geom& g, int par, int j, const int* ent, const int* sv, int Ls,
+                                       long long n5, const void* in, const void* gauge,
+                                       cpx<typename Field<P>::R> (*acc)[12]) {
     typedef typename Field<P>::R R;
-    const int* nb = par ? g.nbr[1] : g.nbr[0];
 #pragma unroll
     for (int dirn = 0; dirn < 2; dirn++) {
-        const int e = __ldg(nb + (2 * MU + dirn) * g.Vh + j);
-        const int jn = e & 0x7fffffff;
+        const int e = EOFA_HOP_PREFETCH ? ent[2 * MU + dirn]
+                                        : __ldg((par ? g.nbr[1] : g.nbr[0]) + (2 * MU + dirn) * g.Vh + j);
+        const int jn = e;
         cpx<R> h[SPT][6];
 #pragma unroll
         for (int k = 0; k < SPT; k++) {
             cpx<R> psi[12];
             Field<P>::load(in, jn, sv[k], Ls, n5, psi);
-            if (dirn == 0) project<MU, DAG ? 1 : -1>(psi, e < 0, h[k]);
-            else project<MU, DAG ? -1 : 1>(psi, e < 0, h[k]);
+            if (dirn == 0) project<MU, DAG ? 1 : -1>(psi, h[k]);
+            else project<MU, DAG ? -1 : 1>(psi, h[k]);
         }
         const long long lidx = dirn == 0 ? (long long)((par * 4 + MU) * g.Vh + j)
                                          : (long long)(((1 - par) * 4 + MU) * g.Vh + jn);
@@ -405,10 +407,18 @@ __global__ void __launch_bounds__(256, SPT == 2 ? 2 : (HASOP ? EOFA_DSLASH_MINB 
 #pragma unroll
             for (int c = 0; c < 12; c++) acc[k][c] = mk(R(0), R(0));
         if (site_ok) {
-            hop_mu<P, DAG, 0, SPT>(g, par, j, sv, Ls, n5, in, gauge, acc);
-            hop_mu<P, DAG, 1, SPT>(g, par, j, sv, Ls, n5, in, gauge, acc);
-            hop_mu<P, DAG, 2, SPT>(g, par, j, sv, Ls, n5, in, gauge, acc);
-            hop_mu<P, DAG, 3, SPT>(g, par, j, sv, Ls, n5, in, gauge, acc);
+            // the eight neighbour entries are loaded up front, so that no
+            // spinor load waits behind the load of its own index
+            const int* nb = par ? g.nbr[1] : g.nbr[0];
+            int ent[8];
+            if (EOFA_HOP_PREFETCH) {
+#pragma unroll
+                for (int d = 0; d < 8; d++) ent[d] = __ldg(nb + d * g.Vh + j);
+            }
+            hop_mu<P, DAG, 0, SPT>(g, par, j, ent, sv, Ls, n5, in, gauge, acc);
+            hop_mu<P, DAG, 1, SPT>(g, par, j, ent, sv, Ls, n5, in, gauge, acc);
+            hop_mu<P, DAG, 2, SPT>(g, par, j, ent, sv, Ls, n5, in, gauge, acc);
+            hop_mu<P, DAG, 3, SPT>(g, par, j, ent, sv, Ls, n5, in, gauge, acc);
         }
         if (HASOP) {
             if (site_ok) {
@@ -545,6 +555,7 @@ __global__ void __launch_bounds__(256) xp_update_kernel(Geom g, const double* sc
 }  // namespace dsl
 
 #include "dslash_bulk.cuh"
+#include "dslash_pipe.cuh"
 
 namespace dsl {
 namespace {
@@ -589,13 +600,16 @@ void launch_with(K k, const eofa_ctx* ctx, const Geom& g, int NS, int spt, size_
     k<<<grid, threads, smem, st>>>(g, par, in, out, gauge, op, y, a_out, b_in, red, slot, NS);
 }
 
-// Staged (bulk-copy) configurations are encoded as CFG_BULK | D << 8 | NS;
-// direct ones as NS * 4 + SPT.
+// Staged (bulk-copy) configurations are encoded as CFG_BULK | D << 8 | NS,
+// pipelined (cp.async) ones as CFG_PIPE | PIPE << 8 | NS, direct ones as
+// NS * 4 + SPT.
 #define CFG_BULK (1 << 20)
+#define CFG_PIPE (1 << 21)
 
 // the EOFA_DSLASH_CONFIG spelling of a configuration
 inline std::string cfg_str(int cfg) {
     if (cfg & CFG_BULK) return std::to_string(cfg & 0xff) + ",1," + std::to_string((cfg >> 8) & 0xf);
+    if (cfg & CFG_PIPE) return std::to_string(cfg & 0xff) + ",1,-" + std::to_string((cfg >> 8) & 0xf);
     return std::to_string(cfg / 4) + "," + std::to_string(cfg % 4);
 }
 
@@ -607,6 +621,28 @@ bool bulk_fits(const Geom& g, int NS, int D, bool hasop, const void* in, const v
     if (P == P16 && g.Ls % 4 != 0) return false;  // scale rows must be 16-byte multiples
     if (((uintptr_t)in & 15) || (y && ((uintptr_t)y & 15))) return false;
     return bulk_plan<P, R>(NS, D, g.Ls, hasop).total_b <= 200 * 1024;
+}
+
+template <int P>
+bool pipe_fits(const Geom& g, int NS, int pipe, bool hasop, const void* in, size_t elem) {
+    if (NS < 1 || pipe < 2 || pipe > 3) return false;
+    const int threads = (NS * g.Ls + 31) / 32 * 32;
+    if (threads > 256 || ((uintptr_t)in & 15)) return false;
+    const size_t smem = (size_t)pipe_stage_bytes<P>(pipe, threads) + (hasop ? (size_t)NS * 12 * (g.Ls + 1) * elem : 0);
+    return smem <= 96 * 1024;
+}
+
+template <int P, typename K>
+void launch_pipe(K k, const eofa_ctx* ctx, const Geom& g, int NS, int pipe, size_t elem, bool hasop, int par,
+                 const void* in, void* out, const void* gauge, const Op5& op, const void* y, double a_out, double b_in,
+                 double* red, int slot, cudaStream_t st) {
+    const int threads = (NS * g.Ls + 31) / 32 * 32;
+    const size_t smem =
+        (size_t)pipe_stage_bytes<P>(pipe, threads) + (hasop ? (size_t)NS * 12 * (g.Ls + 1) * elem : 0);
+    const int ntiles = (g.Vh + NS - 1) / NS;
+    if (smem > 40 * 1024) EOFA_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    unsigned grid = grid_size(k, threads, smem, ntiles, ctx->sms);
+    k<<<grid, threads, smem, st>>>(g, par, in, out, gauge, op, y, a_out, b_in, red, slot, NS);
 }
 
 template <int P, typename K>
@@ -624,6 +660,17 @@ void launch_bulk(K k, const eofa_ctx* ctx, const Geom& g, int NS, int D, bool ha
     k<<<grid, threads, pl.total_b, st>>>(g, par, in, out, gauge, op, y, a_out, b_in, red, slot, NS, D, err);
 }
 
+template <int P, typename KP2, typename KP3>
+void launch_pipe_cfg(KP2 kp2, KP3 kp3, const eofa_ctx* ctx, const Geom& g, int cfg, size_t elem, bool hasop, int par,
+                     const void* in, void* out, const void* gauge, const Op5& op, const void* y, double a_out,
+                     double b_in, double* red, int slot, cudaStream_t st) {
+    const int NS = cfg & 0xff, pipe = (cfg >> 8) & 0xf;
+    if (pipe == 2)
+        launch_pipe<P>(kp2, ctx, g, NS, 2, elem, hasop, par, in, out, gauge, op, y, a_out, b_in, red, slot, st);
+    else
+        launch_pipe<P>(kp3, ctx, g, NS, 3, elem, hasop, par, in, out, gauge, op, y, a_out, b_in, red, slot, st);
+}
+
 // Autotuned configuration, timed once per context and kernel variant with
 // CUDA events on the launching stream: the direct kernel at the heuristic
 // sites per tile NS and its halving / doubling, and the staged kernel at
@@ -631,8 +678,8 @@ void launch_bulk(K k, const eofa_ctx* ctx, const Geom& g, int NS, int D, bool ha
 // only write out and the reduction scratch), so the trial launches are
 // harmless.  Small lattices, and launches during stream capture, use the
 // heuristic direct configuration.
-template <int P, typename K1, typename KB>
-int tuned_cfg(K1 k1, KB kb, const eofa_ctx* ctx, const Geom& g, long long key, int ns0, size_t elem, bool hasop,
+template <int P, typename K1, typename KB, typename KP2, typename KP3>
+int tuned_cfg(K1 k1, KB kb, KP2 kp2, KP3 kp3, const eofa_ctx* ctx, const Geom& g, long long key, int ns0, size_t elem, bool hasop,
               int par, const void* in, void* out, const void* gauge, const Op5& op, const void* y, double a_out,
               double b_in, double* red, int slot, cudaStream_t st) {
     auto direct_ok = [&](int c) {
@@ -642,6 +689,8 @@ int tuned_cfg(K1 k1, KB kb, const eofa_ctx* ctx, const Geom& g, long long key, i
         const int f = ctx->forced_cfg;
         if (f & CFG_BULK) {
             if (bulk_fits<P>(g, f & 0xff, (f >> 8) & 0xf, hasop, in, y)) return f;
+        } else if (f & CFG_PIPE) {
+            if (pipe_fits<P>(g, f & 0xff, (f >> 8) & 0xf, hasop, in, elem)) return f;
         } else if (direct_ok(f / 4)) {
             return (f / 4) * 4 + 1;
         }
@@ -658,6 +707,9 @@ int tuned_cfg(K1 k1, KB kb, const eofa_ctx* ctx, const Geom& g, long long key, i
     for (int c : {ns0 / 2, ns0, ns0 * 2, ns0 * 4})
         for (int d = 2; d <= 4; d++)
             if (bulk_fits<P>(g, c, d, hasop, in, y)) cands.push_back(CFG_BULK | d << 8 | c);
+    for (int c : {ns0 / 2, ns0, ns0 * 2})
+        for (int d = 2; d <= 3; d++)
+            if (pipe_fits<P>(g, c, d, hasop, in, elem)) cands.push_back(CFG_PIPE | d << 8 | c);
     int best = def;
     float best_ms = 1e30f;
     cudaEvent_t e0, e1;
@@ -668,6 +720,9 @@ int tuned_cfg(K1 k1, KB kb, const eofa_ctx* ctx, const Geom& g, long long key, i
             if (cfg & CFG_BULK)
                 launch_bulk<P>(kb, ctx, g, cfg & 0xff, (cfg >> 8) & 0xf, hasop, par, in, out, gauge, op, y, a_out,
                                b_in, red, slot, st);
+            else if (cfg & CFG_PIPE)
+                launch_pipe_cfg<P>(kp2, kp3, ctx, g, cfg, elem, hasop, par, in, out, gauge, op, y, a_out, b_in, red,
+                                   slot, st);
             else
                 launch_with(k1, ctx, g, cfg / 4, 1, elem, hasop, par, in, out, gauge, op, y, a_out, b_in, red, slot,
                             st);
@@ -704,12 +759,19 @@ void launch_dslash_t(const eofa_ctx* ctx, int par, const void* in, void* out, co
     const bool hasop = op.inv[0] || op.inv[1] || op.fwd[0] || op.fwd[1] || op.sigma[0] != 0.0 || op.sigma[1] != 0.0;
     auto k1 = hasop ? dslash_kernel<P, DAG, LS, true, 1> : dslash_kernel<P, DAG, LS, false, 1>;
     auto kb = hasop ? dslash_bulk_kernel<P, DAG, LS, true> : dslash_bulk_kernel<P, DAG, LS, false>;
+    auto kp2 = hasop ? dslash_pipe_kernel<P, DAG, LS, true, 2> : dslash_pipe_kernel<P, DAG, LS, false, 2>;
+    auto kp3 = hasop ? dslash_pipe_kernel<P, DAG, LS, true, 3> : dslash_pipe_kernel<P, DAG, LS, false, 3>;
     const long long key = ((((long long)P * 2 + DAG) * 128 + g.Ls) * 2 + (hasop ? 1 : 0)) * 2 + (y ? 1 : 0);
     const int ns0 = pick_ns(g.Ls, sizeof(cpx<R>));
-    int cfg = tuned_cfg<P>(k1, kb, ctx, g, key, ns0, sizeof(cpx<R>), hasop, par, in, out, gauge, op, y, a_out, b_in,
+    int cfg = tuned_cfg<P>(k1, kb, kp2, kp3, ctx, g, key, ns0, sizeof(cpx<R>), hasop, par, in, out, gauge, op, y, a_out, b_in,
                            red, slot, st);
     if ((cfg & CFG_BULK) && !bulk_fits<P>(g, cfg & 0xff, (cfg >> 8) & 0xf, hasop, in, y)) cfg = ns0 * 4 + 1;
-    if (cfg & CFG_BULK)
+    if ((cfg & CFG_PIPE) && !pipe_fits<P>(g, cfg & 0xff, (cfg >> 8) & 0xf, hasop, in, sizeof(cpx<R>)))
+        cfg = ns0 * 4 + 1;
+    if (cfg & CFG_PIPE)
+        launch_pipe_cfg<P>(kp2, kp3, ctx, g, cfg, sizeof(cpx<R>), hasop, par, in, out, gauge, op, y, a_out, b_in, red,
+                           slot, st);
+    else if (cfg & CFG_BULK)
         launch_bulk<P>(kb, ctx, g, cfg & 0xff, (cfg >> 8) & 0xf, hasop, par, in, out, gauge, op, y, a_out, b_in, red,
                        slot, st);
     else

@@ -98,6 +98,7 @@ struct Prof {
     int used = 0;
     std::vector<cudaEvent_t> ev;  // pairs (start, stop)
     std::vector<int> kind;        // 0..2 hop per precision, 3..5 op5 per precision
+    std::vector<double> bytes;    // algorithmic bytes of each launch
 };
 // ------------------------------------------------------------------ context
 
@@ -138,7 +139,7 @@ struct eofa_ctx {
     } while (0)
 
 extern long long g_launches;
-void prof_begin(const struct eofa_ctx* ctx, int kind, cudaStream_t st);
+void prof_begin(const struct eofa_ctx* ctx, int kind, cudaStream_t st, double bytes = 0.0);
 void prof_end(const struct eofa_ctx* ctx, cudaStream_t st);
 
 struct eofa_error {

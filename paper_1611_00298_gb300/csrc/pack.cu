@@ -52,7 +52,10 @@ __global__ void unpack_kernel(Geom g, int V, const void* even, const void* odd, 
     for (int c = 0; c < 12; c++) dst[c] = make_double2((double)v[c].re, (double)v[c].im);
 }
 
-__global__ void gauge_pack_kernel(Geom g, const double* __restrict__ canon, double2* g64, float2* g32) {
+// The time-boundary phase bc_t multiplies the packed t-links on the last
+// time slice: the forward hop from t = T - 1 and the backward hop from t = 0
+// are the only hops that use them, and both cross the boundary.
+__global__ void gauge_pack_kernel(Geom g, double bc_t, const double* __restrict__ canon, double2* g64, float2* g32) {
     long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     long long nl = 2LL * 4 * g.Vh;
     if (tid >= nl) return;
@@ -61,8 +64,11 @@ __global__ void gauge_pack_kernel(Geom g, const double* __restrict__ canon, doub
     int p = (int)(tid / (4LL * g.Vh));
     int i = cb_to_lex(g, j, p);
     const double2* src = (const double2*)canon + ((long long)i * 4 + mu) * 9;
+    const double ph = (mu == 3 && i / (g.X * g.Y * g.Z) == g.T - 1) ? bc_t : 1.0;
     for (int k = 0; k < 9; k++) {
         double2 z = src[k];
+        z.x *= ph;
+        z.y *= ph;
         g64[tid * 9 + k] = z;
         g32[tid * 10 + k] = make_float2((float)z.x, (float)z.y);
     }
@@ -130,7 +136,8 @@ void launch_unpack(const eofa_ctx* ctx, int prec, const void* even, const void* 
 void launch_gauge_pack(const eofa_ctx* ctx, const double* canon, cudaStream_t st) {
     Geom g = ctx_geom(ctx);
     long long n = 8LL * g.Vh;
-    gauge_pack_kernel<<<blocks(n, 256), 256, 0, st>>>(g, canon, (double2*)ctx->gauge[P64], (float2*)ctx->gauge[P32]);
+    gauge_pack_kernel<<<blocks(n, 256), 256, 0, st>>>(g, (double)ctx->bc_t, canon, (double2*)ctx->gauge[P64],
+                                                      (float2*)ctx->gauge[P32]);
     EOFA_LAUNCHED();
 }
 

@@ -6,11 +6,12 @@ long long g_launches = 0;
 
 #define PROF_PAIRS 65536
 
-void prof_begin(const eofa_ctx* ctx, int kind, cudaStream_t st) {
+void prof_begin(const eofa_ctx* ctx, int kind, cudaStream_t st, double bytes) {
     Prof* p = ctx->prof;
     if (!p || !p->on || p->used >= PROF_PAIRS) return;
     EOFA_CUDA(cudaEventRecord(p->ev[2 * p->used], st));
     p->kind[p->used] = kind;
+    p->bytes[p->used] = bytes;
 }
 
 void prof_end(const eofa_ctx* ctx, cudaStream_t st) {
@@ -31,6 +32,7 @@ int eofa_profile_start(eofa_ctx* ctx) {
             ctx->prof = new Prof();
             ctx->prof->ev.resize(2 * PROF_PAIRS);
             ctx->prof->kind.resize(PROF_PAIRS);
+            ctx->prof->bytes.resize(PROF_PAIRS);
             for (auto& e : ctx->prof->ev) EOFA_CUDA(cudaEventCreate(&e));
         }
         ctx->prof->used = 0;
@@ -46,6 +48,7 @@ int eofa_profile_stop(eofa_ctx* ctx, eofa_profile* out) {
     for (int k = 0; k < 6; k++) {
         out->launches[k] = 0;
         out->ms[k] = 0.0;
+        out->bytes[k] = 0.0;
     }
     Prof* p = ctx->prof;
     if (!p) return EOFA_OK;
@@ -57,6 +60,7 @@ int eofa_profile_stop(eofa_ctx* ctx, eofa_profile* out) {
             EOFA_CUDA(cudaEventElapsedTime(&ms, p->ev[2 * i], p->ev[2 * i + 1]));
             out->launches[p->kind[i]]++;
             out->ms[p->kind[i]] += ms;
+            out->bytes[p->kind[i]] += p->bytes[i];
         }
         p->used = 0;
     } catch (const eofa_error& e) {

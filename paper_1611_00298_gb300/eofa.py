@@ -52,7 +52,7 @@ class SolveParams(ctypes.Structure):
 
 
 class Profile(ctypes.Structure):
-    _fields_ = [("launches", ctypes.c_longlong * 6), ("ms", ctypes.c_double * 6)]
+    _fields_ = [("launches", ctypes.c_longlong * 6), ("ms", ctypes.c_double * 6), ("bytes", ctypes.c_double * 6)]
 
 
 class MDParams(ctypes.Structure):
@@ -363,10 +363,11 @@ class Lattice:
         self._check(self.lib.eofa_profile_start(self.ctx), "profile_start")
 
     def profile_stop(self):
-        """Per-kind (hop FP64/FP32/FP16, 5D-local FP64/FP32/FP16) launch counts and milliseconds."""
+        """Per-kind (hop FP64/FP32/FP16, 5D-local FP64/FP32/FP16) launch counts, milliseconds and
+        algorithmic bytes."""
         pr = Profile()
         self._check(self.lib.eofa_profile_stop(self.ctx, ctypes.byref(pr)), "profile_stop")
-        return list(pr.launches), list(pr.ms)
+        return list(pr.launches), list(pr.ms), list(pr.bytes)
 
     def pseudofermion_solutions_dev(self, phi, chiL, chiR, alpha, M5, m1, m2, precision=PREC_F64, tol=1e-10):
         """chi_L, chi_R of Eq. (5) / (7) into the given device tensors; returns (S, info)."""

@@ -173,11 +173,13 @@ def test_schur_hop_parity(eofa, case, prec, tol):
             assert _rel(got, ref) < tol, (out_par, dag, _rel(got, ref))
 
 
-@pytest.mark.parametrize("cfg", ["2,1", "4,1", "8,1", "8,1,2", "5,1,3", "2,1,4", "10,1,3"])
+@pytest.mark.parametrize("cfg", ["2,1", "4,1", "8,1", "8,1,2", "5,1,3", "2,1,4", "10,1,3", "4,1,-2", "5,1,-3",
+                                 "2,1,-2"])
 def test_forced_dslash_configurations(eofa, cfg, monkeypatch):
     """Every configuration the autotuner may pick gives the same fused kernel
-    result: direct kernel "NS,SPT", staged bulk-copy kernel "NS,SPT,depth";
-    Vh = 96 leaves a ragged last tile for NS = 5 and 10."""
+    result: direct kernel "NS,SPT", staged bulk-copy kernel "NS,SPT,depth",
+    pipelined cp.async kernel "NS,SPT,-slots"; Vh = 96 leaves a ragged last
+    tile for NS = 5 and 10."""
     import torch
     monkeypatch.setenv("EOFA_DSLASH_CONFIG", cfg)
     dims, Ls, alpha, M5, mf, bc = (4, 4, 2, 6), 24, 2.0, 1.8, 0.0362, -1

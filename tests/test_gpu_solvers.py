@@ -60,11 +60,12 @@ def test_dwf_solve_matches_oracle_solution(eofa):
     assert _rel(x, xo) < 1e-10
 
 
-@pytest.mark.parametrize("cfg", ["5,1,2", "2,1,3"])
+@pytest.mark.parametrize("cfg", ["5,1,2", "2,1,3", "5,1,-2", "4,1,-3"])
 def test_solves_with_staged_dslash(eofa, cfg, monkeypatch):
-    """The staged (bulk-copy) dslash, forced for every launch including the
-    solver's fused axpy form, gives the oracle's D_DWF solution in FP64 and
-    a converged mixed-precision EOFA solve (ragged last tile at NS = 5)."""
+    """The staged (bulk-copy) and pipelined (cp.async) dslash kernels, forced
+    for every launch including the solver's fused axpy form, give the
+    oracle's D_DWF solution in FP64 and a converged mixed-precision EOFA
+    solve (ragged last tile at NS = 5)."""
     monkeypatch.setenv("EOFA_DSLASH_CONFIG", cfg)
     dims, Ls = (4, 4, 2, 4), 8
     lat, U = _setup(eofa, dims, Ls, eps=0.5)
