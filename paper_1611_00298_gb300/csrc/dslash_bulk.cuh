@@ -215,6 +215,8 @@ __global__ void __launch_bounds__(BULK_MAX_THREADS, 2) dslash_bulk_kernel(
     const int nd = y != nullptr ? 9 : 8;      // stages per tile
     const long long n5 = (long long)g.Vh * Ls;
     const int ntiles = (g.Vh + NS - 1) / NS;
+    __shared__ R wv_s[HASOP ? 4 * EOFA_MAX_LS : 1];
+    if (HASOP) stage_wv<R>(op, Ls, wv_s);  // the barrier after the mbarrier set-up covers it
     if (threadIdx.x == 0) {
         for (int k = 0; k < D; k++) {
             mbar_init(smem_addr(full + k), 1);
@@ -344,7 +346,7 @@ __global__ void __launch_bounds__(BULK_MAX_THREADS, 2) dslash_bulk_kernel(
                 }
                 consumer_sync(NC);
                 for (int idx = threadIdx.x; idx < nsites * 12; idx += NC)
-                    column_op<R, LS>(op, idx % 12, col + idx * LsP, Ls);
+                    column_op<R, LS>(op, idx % 12, col + idx * LsP, Ls, wv_s);
                 consumer_sync(NC);
                 if (site_ok) {
 #pragma unroll

@@ -191,11 +191,24 @@ template <typename R>
 struct Half {
     int inv, fwd, dir1, dir2;
     R p1, q1, p2, q2, sigma, mass, mr, invp, invN;
-    const double *w, *v;
+    const R *w, *v;  // rank-one vectors, staged in shared memory
 };
 
+// The rank-one vectors w, v of both chiralities, converted to R once per
+// block into shared memory wv[4 * Ls] (layout [h][w, v][s]); callers
+// synchronise the block before the first column_op.
 template <typename R>
-__device__ __forceinline__ Half<R> half_of(const Op5& op, int h) {
+__device__ __forceinline__ void stage_wv(const Op5& op, int Ls, R* wv) {
+    for (int i = threadIdx.x; i < 4 * Ls; i += blockDim.x) {
+        const int h = i / (2 * Ls), which = (i / Ls) & 1, s = i % Ls;
+        const double* src = which ? (h ? op.v[1] : op.v[0]) : (h ? op.w[1] : op.w[0]);
+        const double sg = h ? op.sigma[1] : op.sigma[0];
+        wv[i] = (sg != 0.0 && src) ? (R)src[s] : R(0);
+    }
+}
+
+template <typename R>
+__device__ __forceinline__ Half<R> half_of(const Op5& op, int h, const R* wv, int Ls) {
     Half<R> H;
     H.inv = h ? op.inv[1] : op.inv[0];
     H.fwd = h ? op.fwd[1] : op.fwd[0];
@@ -210,8 +223,8 @@ __device__ __forceinline__ Half<R> half_of(const Op5& op, int h) {
     H.mr = (R)(h ? op.mr[1] : op.mr[0]);
     H.invp = (R)(h ? op.invp[1] : op.invp[0]);
     H.invN = (R)(h ? op.invN[1] : op.invN[0]);
-    H.w = h ? op.w[1] : op.w[0];
-    H.v = h ? op.v[1] : op.v[0];
+    H.w = wv + (2 * h) * Ls;
+    H.v = wv + (2 * h + 1) * Ls;
     return H;
 }
 
@@ -256,11 +269,11 @@ __device__ __forceinline__ void col_stream(const Half<R>& H, cpx<R>* col) {
         acc = mr * acc;
         const cpx<R> u0 = invN * (lds(col) - mass * acc);
         cpx<R> u = u0;
-        if (R1) d = (R)__ldg(H.v) * u0;
+        if (R1) d = H.v[0] * u0;
 #pragma unroll
         for (int s = 1; s < LS; s++) {
             const cpx<R> un = invp * (lds(col + s) - q * u);
-            if (R1) d = d + (R)__ldg(H.v + s) * un;
+            if (R1) d = d + H.v[s] * un;
             sts(col + s, p2 * un + q2 * u);
             u = un;
         }
@@ -271,11 +284,11 @@ __device__ __forceinline__ void col_stream(const Half<R>& H, cpx<R>* col) {
         acc = mr * acc;
         const cpx<R> uL = invN * (lds(col + LS - 1) - mass * acc);
         cpx<R> u = uL;
-        if (R1) d = (R)__ldg(H.v + LS - 1) * uL;
+        if (R1) d = H.v[LS - 1] * uL;
 #pragma unroll
         for (int s = LS - 2; s >= 0; s--) {
             const cpx<R> un = invp * (lds(col + s) - q * u);
-            if (R1) d = d + (R)__ldg(H.v + s) * un;
+            if (R1) d = d + H.v[s] * un;
             sts(col + s, p2 * un + q2 * u);
             u = un;
         }
@@ -285,14 +298,14 @@ __device__ __forceinline__ void col_stream(const Half<R>& H, cpx<R>* col) {
         // rank-one term: out += sigma w (v . u), u the inverse's result
         const cpx<R> sd = H.sigma * d;
 #pragma unroll
-        for (int s = 0; s < LS; s++) sts(col + s, lds(col + s) + (R)__ldg(H.w + s) * sd);
+        for (int s = 0; s < LS; s++) sts(col + s, lds(col + s) + H.w[s] * sd);
     }
 }
 
 // apply B to the column at col (shared memory, stride 1, length Ls)
 template <typename R, int LS>
-__device__ __forceinline__ void column_op(const Op5& op, int c, cpx<R>* col, int Ls) {
-    const Half<R> H = half_of<R>(op, c < 6 ? 0 : 1);
+__device__ __forceinline__ void column_op(const Op5& op, int c, cpx<R>* col, int Ls, const R* wv) {
+    const Half<R> H = half_of<R>(op, c < 6 ? 0 : 1, wv, Ls);
     if (LS > 0 && H.inv && (!H.fwd || H.dir2 == H.dir1)) {
         if (H.sigma == R(0)) col_stream<R, (LS > 0 ? LS : 1), false>(H, col);
         else col_stream<R, (LS > 0 ? LS : 1), true>(H, col);
@@ -301,11 +314,11 @@ __device__ __forceinline__ void column_op(const Op5& op, int c, cpx<R>* col, int
     if (H.inv) sm_inv<R>(col, Ls, H.p1, H.q1, H.dir1, H.mass);
     cpx<R> d = mk(R(0), R(0));
     if (H.sigma != R(0))
-        for (int s = 0; s < Ls; s++) d = d + (R)__ldg(H.v + s) * col[s];
+        for (int s = 0; s < Ls; s++) d = d + H.v[s] * col[s];
     if (H.fwd) sm_fwd<R>(col, Ls, H.p2, H.q2, H.dir2, H.mass);
     if (H.sigma != R(0)) {
         const cpx<R> sd = H.sigma * d;
-        for (int s = 0; s < Ls; s++) col[s] = col[s] + (R)__ldg(H.w + s) * sd;
+        for (int s = 0; s < Ls; s++) col[s] = col[s] + H.w[s] * sd;
     }
 }
 
@@ -389,6 +402,11 @@ __global__ void __launch_bounds__(256, SPT == 2 ? 2 : (HASOP ? EOFA_DSLASH_MINB 
     const int Ls = LS > 0 ? LS : g.Ls;
     const int LsP = Ls + 1;
     const int Lt = Ls / SPT;  // threads per site
+    __shared__ R wv_s[HASOP ? 4 * EOFA_MAX_LS : 1];
+    if (HASOP) {
+        stage_wv<R>(op, Ls, wv_s);
+        __syncthreads();
+    }
     const long long n5 = (long long)g.Vh * Ls;
     const int ls = threadIdx.x / Lt, sh = threadIdx.x - ls * Lt;
     int sv[SPT];
@@ -430,7 +448,7 @@ __global__ void __launch_bounds__(256, SPT == 2 ? 2 : (HASOP ? EOFA_DSLASH_MINB 
             __syncthreads();
             const int nsites = min(NS, g.Vh - tile * NS);
             for (int idx = threadIdx.x; idx < nsites * 12; idx += blockDim.x)
-                column_op<R, LS>(op, idx % 12, sm + idx * LsP, Ls);
+                column_op<R, LS>(op, idx % 12, sm + idx * LsP, Ls, wv_s);
             __syncthreads();
             if (site_ok) {
 #pragma unroll
@@ -477,6 +495,11 @@ __global__ void __launch_bounds__(256, 3) local5_kernel(Geom g, Op5 op, const vo
     const bool ident = op_is_identity(op);
     const int ntiles = (g.Vh + NS - 1) / NS;
     const R c = (R)(use_alpha ? -cg_alpha(sc, it) : c0);
+    __shared__ R wv_s[4 * EOFA_MAX_LS];
+    if (out && !ident) {
+        stage_wv<R>(op, Ls, wv_s);
+        __syncthreads();
+    }
     double nacc = 0.0;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int j = tile * NS + ls;
@@ -502,7 +525,7 @@ __global__ void __launch_bounds__(256, 3) local5_kernel(Geom g, Op5 op, const vo
                 __syncthreads();
                 const int nsites = min(NS, g.Vh - tile * NS);
                 for (int idx = threadIdx.x; idx < nsites * 12; idx += blockDim.x)
-                    column_op<R, LS>(op, idx % 12, sm + idx * LsP, Ls);
+                    column_op<R, LS>(op, idx % 12, sm + idx * LsP, Ls, wv_s);
                 __syncthreads();
                 if (site_ok) {
 #pragma unroll

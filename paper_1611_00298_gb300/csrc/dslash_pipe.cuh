@@ -146,6 +146,11 @@ __global__ void __launch_bounds__(256, EOFA_PIPE_MINB) dslash_pipe_kernel(
     const int ntiles = (g.Vh + NS - 1) / NS;
     const R scale = (R)(-0.5 * a_out);
     const int* nb = par ? g.nbr[1] : g.nbr[0];
+    __shared__ R wv_s[HASOP ? 4 * EOFA_MAX_LS : 1];
+    if (HASOP) {
+        stage_wv<R>(op, Ls, wv_s);
+        __syncthreads();
+    }
     double nacc = 0.0;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int j = tile * NS + ls;
@@ -179,7 +184,7 @@ __global__ void __launch_bounds__(256, EOFA_PIPE_MINB) dslash_pipe_kernel(
             __syncthreads();
             const int nsites = min(NS, g.Vh - tile * NS);
             for (int idx = threadIdx.x; idx < nsites * 12; idx += blockDim.x)
-                column_op<R, LS>(op, idx % 12, sm + idx * LsP, Ls);
+                column_op<R, LS>(op, idx % 12, sm + idx * LsP, Ls, wv_s);
             __syncthreads();
             if (site_ok) {
 #pragma unroll
