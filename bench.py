@@ -257,7 +257,8 @@ def hmc_bench(args):
     out["force_rms"] = {"L": rms(FL), "R": rms(FR)}
     out["force_max"] = {"L": float(FL.abs().amax()), "R": float(FR.abs().amax())}
     for name, extra in (("nested", dict(nsteps=4, n_inner=2)),
-                        ("split_lr", dict(nsteps=2, n_middle=2, n_inner=2, split_lr=True))):
+                        ("split_R_outer", dict(nsteps=2, n_middle=2, n_inner=2, split_lr=1)),
+                        ("split_L_outer", dict(nsteps=2, n_middle=2, n_inner=2, split_lr=2))):
         lat.gauge_load(U)
         P = torch.from_numpy(P0).cuda()
         torch.cuda.synchronize()
@@ -538,7 +539,7 @@ def kernel_version():
     """Hash of the dslash kernel sources, to invalidate stored ncu traffic when they change."""
     import hashlib
     h = hashlib.sha256()
-    for f in ("dslash_impl.cuh", "dslash_bulk.cuh", "field.cuh"):
+    for f in ("dslash_impl.cuh", "dslash_bulk.cuh", "dslash_pipe.cuh", "field.cuh"):
         h.update(open(os.path.join(ROOT, "paper_1611_00298_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 

@@ -251,10 +251,11 @@ int eofa_gauge_force_dev(eofa_ctx* ctx, double beta, const double* U_dev, double
  * where P~ kicks with the force at exp(-i z F(U)) U, z = h^2/24 (PQPQP) or
  * (2 - sqrt 3) h^2/12 (QPQPQ).  n_inner > 0 nests the gauge force: the EOFA
  * force sits on the outer level and every outer drift is n_inner steps of
- * the same scheme for S_g.  split_lr = 1 integrates the two terms of Eq. (5)
- * on separate time scales (Sexton-Weingarten): the S_R force on the outer
- * level, the S_L force with n_middle steps per outer drift, the gauge force
- * with n_inner steps per S_L drift (beta = 0: no gauge level).  phi_dev =
+ * the same scheme for S_g.  split_lr = 1 or 2 integrates the two terms of
+ * Eq. (5) on separate time scales (Sexton-Weingarten): one EOFA term on the
+ * outer level (S_R for 1, S_L for 2), the other with n_middle steps per outer
+ * drift, the gauge force with n_inner steps per middle drift (beta = 0: no
+ * gauge level); the larger force belongs on the finer level.  phi_dev =
  * NULL integrates the gauge action alone (n_inner must then be 0); beta = 0
  * drops the gauge action. */
 #define EOFA_INT_LEAPFROG 0
@@ -270,8 +271,8 @@ typedef struct {
     int nsteps;      /* outer steps */
     double tau;      /* trajectory length */
     int n_inner;     /* gauge steps per drift of the level above (0: one level) */
-    int split_lr;    /* 1: S_R force outermost, S_L force in the middle (Sec. 3.3 asymmetry) */
-    int n_middle;    /* with split_lr: S_L steps per outer drift */
+    int split_lr;    /* 1: S_R force outermost, S_L in the middle; 2: S_L outermost, S_R in the middle */
+    int n_middle;    /* with split_lr: steps of the middle force per outer drift */
 } eofa_md_params;
 typedef struct {
     double H0, dH;  /* H at the start, H(end) - H(start) */

@@ -191,14 +191,16 @@ def trajectory(U, P, forces, tau, nsteps, scheme="qpqpq", n_inner=0):
     return trajectory_levels(U, P, levels, forces.energy, tau, scheme)
 
 
-def split_lr_trajectory(U, P, beta, fermion, tau, nsteps, n_middle, n_inner, scheme="qpqpq"):
+def split_lr_trajectory(U, P, beta, fermion, tau, nsteps, n_middle, n_inner, scheme="qpqpq", outer="R"):
     """Asymmetric EOFA integration (Sexton-Weingarten over the two terms of
-    Eq. (5)): the P_+ (S_R) force on the outer level, the P_- (S_L) force in
-    the middle, the gauge force innermost (omitted when beta = 0)."""
+    Eq. (5)): one term's force (outer = 'R': S_R, 'L': S_L) on the outer
+    level, the other in the middle, the gauge force innermost (omitted when
+    beta = 0)."""
     f = fermion
     args = (f["phi"], f["Ls"], f["alpha"], f["M5"], f["m1"], f["m2"], f["bc_t"])
-    levels = [(lambda U_: oeofa.force_part(U_, *args, "R", f["tol"]), nsteps),
-              (lambda U_: oeofa.force_part(U_, *args, "L", f["tol"]), n_middle)]
+    inner_part = "L" if outer == "R" else "R"
+    levels = [(lambda U_: oeofa.force_part(U_, *args, outer, f["tol"]), nsteps),
+              (lambda U_: oeofa.force_part(U_, *args, inner_part, f["tol"]), n_middle)]
     if beta != 0.0:
         levels.append((lambda U_: force(U_, beta), n_inner))
     forces = Forces(beta, fermion)

@@ -81,7 +81,8 @@ std::complex<double> cdot(eofa_ctx* ctx, long long n, const double* a, const dou
 }
 
 // Solve G c = r (m x m complex) by Gaussian elimination with partial pivoting;
-// false when the Gram matrix is numerically singular.
+// false when the Gram matrix is numerically singular (a pivot below 1e-13 of
+// the largest diagonal entry).
 bool small_solve(std::vector<std::complex<double>> G, std::vector<std::complex<double>>& r, int m) {
     double scale = 0;
     for (int i = 0; i < m; i++) scale = std::fmax(scale, std::abs(G[i * m + i]));
@@ -178,11 +179,20 @@ extern "C" int eofa_heatbath_dev(eofa_ctx* ctx, int Ls, double alpha, double M5,
                             Gm[j * m + i] = std::conj(Gm[i * m + j]);
                         }
                     }
-                    if (small_solve(Gm, r, m)) {
+                    // nearly dependent history makes the normal equations singular:
+                    // drop the oldest solutions until the system is solvable
+                    for (int kk = m; kk >= 1 && !p.use_x0; kk--) {
+                        const int o = m - kk;  // first kept vector
+                        std::vector<std::complex<double>> Gk(kk * kk), rk(kk);
+                        for (int i = 0; i < kk; i++) {
+                            rk[i] = r[o + i];
+                            for (int j = 0; j < kk; j++) Gk[i * kk + j] = Gm[(o + i) * m + (o + j)];
+                        }
+                        if (!small_solve(Gk, rk, kk)) continue;
                         EOFA_CUDA(cudaMemsetAsync(x, 0, b5, st));
-                        for (int i = 0; i < m; i++) {
-                            flat_caxpy_kernel<<<nblk(n5, 256), 256, 0, st>>>(n5, r[i].real(), r[i].imag(),
-                                                                             (const double2*)prev[l - m + i],
+                        for (int i = 0; i < kk; i++) {
+                            flat_caxpy_kernel<<<nblk(n5, 256), 256, 0, st>>>(n5, rk[i].real(), rk[i].imag(),
+                                                                             (const double2*)prev[l - kk + i],
                                                                              (double2*)x);
                             EOFA_LAUNCHED();
                         }

@@ -97,7 +97,8 @@ int eofa_leapfrog_dev(eofa_ctx* ctx, int Ls, double alpha, double M5, double m1,
 // a level's displacement uses its own force only (the forces commute):
 //   one level:     EOFA + gauge (or gauge alone without phi)
 //   n_inner > 0:   EOFA | gauge
-//   split_lr:      S_R force | S_L force | gauge (asymmetric L/R integration)
+//   split_lr = 1:  S_R force | S_L force | gauge (asymmetric L/R integration)
+//   split_lr = 2:  S_L force | S_R force | gauge
 enum Force { F_EOFA_AND_GAUGE, F_EOFA, F_EOFA_L, F_EOFA_R, F_GAUGE };
 
 struct Trajectory {
@@ -123,7 +124,8 @@ struct Trajectory {
             kind = {F_GAUGE};
             nsub = {p.nsteps};
         } else if (p.split_lr) {
-            kind = {F_EOFA_R, F_EOFA_L};
+            // 1: S_R outermost, S_L in the middle; 2: the reverse
+            kind = p.split_lr == 2 ? std::vector<Force>{F_EOFA_L, F_EOFA_R} : std::vector<Force>{F_EOFA_R, F_EOFA_L};
             nsub = {p.nsteps, p.n_middle};
             if (p.beta != 0.0) {
                 kind.push_back(F_GAUGE);
@@ -224,7 +226,8 @@ struct Trajectory {
 extern "C" int eofa_hmc_trajectory_dev(eofa_ctx* ctx, const eofa_md_params* p, const double* phi_dev, double* P_dev,
                                        double* U_dev, eofa_md_info* info, void* stream) {
     if (!ctx || !p || !P_dev || !info) return fail(ctx, EOFA_EINVAL, "null argument");
-    const bool bad_split = p->split_lr && (!phi_dev || p->n_middle < 1 || (p->beta != 0.0 && p->n_inner < 1));
+    const bool bad_split = p->split_lr < 0 || p->split_lr > 2 ||
+                           (p->split_lr && (!phi_dev || p->n_middle < 1 || (p->beta != 0.0 && p->n_inner < 1)));
     if (p->nsteps < 1 || !(p->tau > 0) || p->n_inner < 0 || p->integrator < EOFA_INT_LEAPFROG ||
         p->integrator > EOFA_INT_FG_QPQPQ || (!p->split_lr && p->n_inner > 0 && (!phi_dev || p->beta == 0.0)) ||
         (!phi_dev && p->beta == 0.0) || bad_split)

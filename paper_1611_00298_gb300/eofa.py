@@ -428,7 +428,7 @@ class Lattice:
                            split_lr=False, n_middle=0):
         """One MD trajectory (P and the context's links updated in place); returns the info dict."""
         prm = MDParams(self.Ls, alpha, M5, m1, m2, precision, tol, beta, integrator, nsteps, tau, n_inner,
-                       int(split_lr), n_middle)
+                       int(split_lr), n_middle)  # split_lr: 0 / False, 1 / True (S_R outer), 2 (S_L outer)
         info = MDInfo()
         rc = self.lib.eofa_hmc_trajectory_dev(self.ctx, ctypes.byref(prm), _ptr(phi) if phi is not None else None,
                                               _ptr(P), _ptr(U) if U is not None else None, ctypes.byref(info),

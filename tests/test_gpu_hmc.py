@@ -151,8 +151,9 @@ def test_force_parts_match_oracle(eofa):
     lat.close()
 
 
-def test_split_lr_trajectory_matches_oracle(eofa):
-    """Asymmetric integration: S_R force outermost, S_L force in the middle, gauge innermost."""
+@pytest.mark.parametrize("order,outer", [(1, "R"), (2, "L")])
+def test_split_lr_trajectory_matches_oracle(eofa, order, outer):
+    """Asymmetric integration: one EOFA term outermost, the other in the middle, gauge innermost."""
     import torch
     dims, Ls = (2, 2, 2, 2), 4
     U = inputs.gauge_field(dims, 0.4, 23)
@@ -163,11 +164,11 @@ def test_split_lr_trajectory_matches_oracle(eofa):
     Pd = _dev(P)
     Ud = torch.empty_like(Pd)
     info = lat.hmc_trajectory_dev(Pd, _dev(phi), Ud, alpha=ALPHA, M5=M5, m1=M1, m2=M2, tol=1e-13, beta=BETA,
-                                  integrator=eofa.INT_FG_QPQPQ, nsteps=1, tau=0.4, n_inner=1, split_lr=True,
+                                  integrator=eofa.INT_FG_QPQPQ, nsteps=1, tau=0.4, n_inner=1, split_lr=order,
                                   n_middle=2)
     ferm = dict(phi=phi, Ls=Ls, alpha=ALPHA, M5=M5, m1=M1, m2=M2, bc_t=-1.0, tol=1e-13)
-    U1, P1, dH = gauge.split_lr_trajectory(U, P, BETA, ferm, 0.4, 1, 2, 1, "qpqpq")
-    # 4 S_R forces (two displaced kicks) + 3 drifts x 2 steps x 4 S_L forces
+    U1, P1, dH = gauge.split_lr_trajectory(U, P, BETA, ferm, 0.4, 1, 2, 1, "qpqpq", outer=outer)
+    # 4 outer forces (two displaced kicks) + 3 drifts x 2 steps x 4 middle forces
     assert info["fermion_forces"] == 28
     assert np.abs(Ud.cpu().numpy() - U1).max() < 1e-10
     assert np.abs(Pd.cpu().numpy() - P1).max() < 1e-9
