@@ -257,8 +257,8 @@ def hmc_bench(args):
     out["force_rms"] = {"L": rms(FL), "R": rms(FR)}
     out["force_max"] = {"L": float(FL.abs().amax()), "R": float(FR.abs().amax())}
     for name, extra in (("nested", dict(nsteps=4, n_inner=2)),
-                        ("split_R_outer", dict(nsteps=2, n_middle=2, n_inner=2, split_lr=1)),
-                        ("split_L_outer", dict(nsteps=2, n_middle=2, n_inner=2, split_lr=2))):
+                        ("split_R_outer", dict(nsteps=4, n_middle=1, n_inner=2, split_lr=1)),
+                        ("split_L_outer", dict(nsteps=4, n_middle=1, n_inner=2, split_lr=2))):
         lat.gauge_load(U)
         P = torch.from_numpy(P0).cuda()
         torch.cuda.synchronize()
