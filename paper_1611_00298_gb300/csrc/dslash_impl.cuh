@@ -23,6 +23,7 @@
 
 #include <cstdio>
 #include <cstdlib>
+#include <type_traits>
 
 // minimum resident blocks of 256 threads per SM requested from the register
 // allocator (3 -> at most 85 registers, 8 blocks of 96 threads per SM)
@@ -31,6 +32,11 @@
 #endif
 #ifndef EOFA_HOP_MINB
 #define EOFA_HOP_MINB 3
+#endif
+// 1: the axpy input y and the output of the fused dslash use streaming
+// (evict-first) cache hints, leaving L2 to the neighbour spinors
+#ifndef EOFA_STREAM_HINTS
+#define EOFA_STREAM_HINTS 1
 #endif
 // 1: load the eight neighbour entries of a site before its first spinor load
 #ifndef EOFA_HOP_PREFETCH
@@ -302,13 +308,88 @@ __device__ __forceinline__ void col_stream(const Half<R>& H, cpx<R>* col) {
     }
 }
 
+// FP32 form of col_stream on packed pairs: every step multiplies a complex
+// number by real coefficients, so (re, im) travel as one 64-bit register and
+// each complex multiply-add is one f32x2 instruction.
+#ifndef EOFA_PACKED_F32
+#define EOFA_PACKED_F32 1
+#endif
+typedef unsigned long long f2p;
+__device__ __forceinline__ f2p splat2(float a) {
+    f2p r;
+    asm("mov.b64 %0, {%1, %1};" : "=l"(r) : "f"(a));
+    return r;
+}
+__device__ __forceinline__ f2p fma2(f2p a, f2p b, f2p c) {
+    f2p r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+__device__ __forceinline__ f2p mul2(f2p a, f2p b) {
+    f2p r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2p ld2(const cpx<float>* p) { return *reinterpret_cast<const f2p*>(p); }
+__device__ __forceinline__ void st2(cpx<float>* p, f2p v) { *reinterpret_cast<f2p*>(p) = v; }
+
+template <int LS, bool R1>
+__device__ __forceinline__ void col_stream_f2(const Half<float>& H, cpx<float>* col) {
+    const f2p MR = splat2(H.mr), NM = splat2(-H.mass), INVN = splat2(H.invN), NQ = splat2(-H.q1),
+              INVP = splat2(H.invp);
+    const float p2 = H.fwd ? H.p2 : 1.f, q2 = H.fwd ? H.q2 : 0.f;
+    const f2p P2 = splat2(p2), Q2 = splat2(q2), Q2M = splat2(-q2 * H.mass);
+    f2p acc = 0ull, d = 0ull;
+    if (H.dir1 == 0) {
+#pragma unroll
+        for (int s = 1; s < LS; s++) acc = fma2(MR, acc, ld2(col + s));
+        acc = mul2(MR, acc);
+        const f2p u0 = mul2(INVN, fma2(NM, acc, ld2(col)));
+        f2p u = u0;
+        if (R1) d = mul2(splat2(H.v[0]), u0);
+#pragma unroll
+        for (int s = 1; s < LS; s++) {
+            const f2p un = mul2(INVP, fma2(NQ, u, ld2(col + s)));
+            if (R1) d = fma2(splat2(H.v[s]), un, d);
+            st2(col + s, fma2(P2, un, mul2(Q2, u)));
+            u = un;
+        }
+        st2(col, fma2(P2, u0, mul2(Q2M, u)));
+    } else {
+#pragma unroll
+        for (int s = LS - 2; s >= 0; s--) acc = fma2(MR, acc, ld2(col + s));
+        acc = mul2(MR, acc);
+        const f2p uL = mul2(INVN, fma2(NM, acc, ld2(col + LS - 1)));
+        f2p u = uL;
+        if (R1) d = mul2(splat2(H.v[LS - 1]), uL);
+#pragma unroll
+        for (int s = LS - 2; s >= 0; s--) {
+            const f2p un = mul2(INVP, fma2(NQ, u, ld2(col + s)));
+            if (R1) d = fma2(splat2(H.v[s]), un, d);
+            st2(col + s, fma2(P2, un, mul2(Q2, u)));
+            u = un;
+        }
+        st2(col + LS - 1, fma2(P2, uL, mul2(Q2M, u)));
+    }
+    if (R1) {
+        const f2p sd = mul2(splat2(H.sigma), d);
+#pragma unroll
+        for (int s = 0; s < LS; s++) st2(col + s, fma2(splat2(H.w[s]), sd, ld2(col + s)));
+    }
+}
+
 // apply B to the column at col (shared memory, stride 1, length Ls)
 template <typename R, int LS>
 __device__ __forceinline__ void column_op(const Op5& op, int c, cpx<R>* col, int Ls, const R* wv) {
     const Half<R> H = half_of<R>(op, c < 6 ? 0 : 1, wv, Ls);
     if (LS > 0 && H.inv && (!H.fwd || H.dir2 == H.dir1)) {
-        if (H.sigma == R(0)) col_stream<R, (LS > 0 ? LS : 1), false>(H, col);
-        else col_stream<R, (LS > 0 ? LS : 1), true>(H, col);
+        if constexpr (EOFA_PACKED_F32 && std::is_same<R, float>::value) {
+            if (H.sigma == R(0)) col_stream_f2<(LS > 0 ? LS : 1), false>(H, col);
+            else col_stream_f2<(LS > 0 ? LS : 1), true>(H, col);
+        } else {
+            if (H.sigma == R(0)) col_stream<R, (LS > 0 ? LS : 1), false>(H, col);
+            else col_stream<R, (LS > 0 ? LS : 1), true>(H, col);
+        }
         return;
     }
     if (H.inv) sm_inv<R>(col, Ls, H.p1, H.q1, H.dir1, H.mass);
@@ -464,12 +545,14 @@ __global__ void __launch_bounds__(256, SPT == 2 ? 2 : (HASOP ? EOFA_DSLASH_MINB 
                 for (int c = 0; c < 12; c++) acc[k][c] = scale * acc[k][c];
                 if (y != nullptr) {
                     cpx<R> yv[12];
-                    Field<P>::load(y, j, sv[k], Ls, n5, yv);
+                    if (EOFA_STREAM_HINTS) Field<P>::load_stream(y, j, sv[k], Ls, n5, yv);
+                    else Field<P>::load(y, j, sv[k], Ls, n5, yv);
                     const R bb = (R)b_in;
 #pragma unroll
                     for (int c = 0; c < 12; c++) acc[k][c] = acc[k][c] + bb * yv[c];
                 }
-                Field<P>::store(out, j, sv[k], Ls, n5, acc[k]);
+                if (EOFA_STREAM_HINTS) Field<P>::store_stream(out, j, sv[k], Ls, n5, acc[k]);
+                else Field<P>::store(out, j, sv[k], Ls, n5, acc[k]);
                 if (red) nacc += site_norm2<R>(acc[k]);
             }
         }

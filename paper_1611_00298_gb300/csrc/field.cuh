@@ -24,6 +24,22 @@ struct Field<P64> {
 #pragma unroll
         for (int c = 0; c < 12; c++) b[c * Ls] = make_double2(v[c].re, v[c].im);
     }
+    // read-once / write-once forms with the streaming cache hint (evict first)
+    static __device__ __forceinline__ void load_stream(const void* base, int j, int s, int Ls, long long n5,
+                                                       cpx<double> v[12]) {
+        const double2* b = (const double2*)base + (long long)j * 12 * Ls + s;
+#pragma unroll
+        for (int c = 0; c < 12; c++) {
+            double2 t = __ldcs(b + c * Ls);
+            v[c] = mk(t.x, t.y);
+        }
+    }
+    static __device__ __forceinline__ void store_stream(void* base, int j, int s, int Ls, long long n5,
+                                                        const cpx<double> v[12]) {
+        double2* b = (double2*)base + (long long)j * 12 * Ls + s;
+#pragma unroll
+        for (int c = 0; c < 12; c++) __stcs(b + c * Ls, make_double2(v[c].re, v[c].im));
+    }
 };
 
 template <>
@@ -45,6 +61,23 @@ struct Field<P32> {
 #pragma unroll
         for (int k = 0; k < 6; k++)
             b[k * Ls] = make_float4(v[2 * k].re, v[2 * k].im, v[2 * k + 1].re, v[2 * k + 1].im);
+    }
+    static __device__ __forceinline__ void load_stream(const void* base, int j, int s, int Ls, long long n5,
+                                                       cpx<float> v[12]) {
+        const float4* b = (const float4*)base + (long long)j * 6 * Ls + s;
+#pragma unroll
+        for (int k = 0; k < 6; k++) {
+            float4 t = __ldcs(b + k * Ls);
+            v[2 * k] = mk(t.x, t.y);
+            v[2 * k + 1] = mk(t.z, t.w);
+        }
+    }
+    static __device__ __forceinline__ void store_stream(void* base, int j, int s, int Ls, long long n5,
+                                                        const cpx<float> v[12]) {
+        float4* b = (float4*)base + (long long)j * 6 * Ls + s;
+#pragma unroll
+        for (int k = 0; k < 6; k++)
+            __stcs(b + k * Ls, make_float4(v[2 * k].re, v[2 * k].im, v[2 * k + 1].re, v[2 * k + 1].im));
     }
 };
 
@@ -92,6 +125,14 @@ struct Field<P16> {
             b[k * Ls] = make_uint4(w[0], w[1], w[2], w[3]);
         }
         ((float*)((char*)base + n5 * 48))[(long long)j * Ls + s] = sc;
+    }
+    static __device__ __forceinline__ void load_stream(const void* base, int j, int s, int Ls, long long n5,
+                                                       cpx<float> v[12]) {
+        load(base, j, s, Ls, n5, v);
+    }
+    static __device__ __forceinline__ void store_stream(void* base, int j, int s, int Ls, long long n5,
+                                                        const cpx<float> v[12]) {
+        store(base, j, s, Ls, n5, v);
     }
 };
 
