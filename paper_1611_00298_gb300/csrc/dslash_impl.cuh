@@ -589,14 +589,19 @@ __global__ void __launch_bounds__(256, 3) local5_kernel(Geom g, Op5 op, const vo
         const bool site_ok = active_thread && j < g.Vh;
         cpx<R> v[12];
         if (site_ok) {
-            Field<P>::load(x, j, s, Ls, n5, v);
+            if (EOFA_STREAM_HINTS) Field<P>::load_stream(x, j, s, Ls, n5, v);
+            else Field<P>::load(x, j, s, Ls, n5, v);
             if (z != nullptr) {
                 cpx<R> zv[12];
-                Field<P>::load(z, j, s, Ls, n5, zv);
+                if (EOFA_STREAM_HINTS) Field<P>::load_stream(z, j, s, Ls, n5, zv);
+                else Field<P>::load(z, j, s, Ls, n5, zv);
 #pragma unroll
                 for (int k = 0; k < 12; k++) v[k] = v[k] + c * zv[k];
             }
-            if (xw) Field<P>::store(xw, j, s, Ls, n5, v);
+            if (xw) {
+                if (EOFA_STREAM_HINTS) Field<P>::store_stream(xw, j, s, Ls, n5, v);
+                else Field<P>::store(xw, j, s, Ls, n5, v);
+            }
             if (red) nacc += site_norm2<R>(v);
         }
         if (out) {
@@ -618,7 +623,8 @@ __global__ void __launch_bounds__(256, 3) local5_kernel(Geom g, Op5 op, const vo
             if (site_ok) {
 #pragma unroll
                 for (int k = 0; k < 12; k++) v[k] = (R)a_out * v[k];
-                Field<P>::store(out, j, s, Ls, n5, v);
+                if (EOFA_STREAM_HINTS) Field<P>::store_stream(out, j, s, Ls, n5, v);
+                else Field<P>::store(out, j, s, Ls, n5, v);
             }
             if (!ident) __syncthreads();
         }
