@@ -74,9 +74,38 @@ __device__ __forceinline__ void link_row<double>(const void* g, long long idx, i
     }
 }
 
+// 1: a forward FP32 link row (three consecutive elements of the 80-byte
+// record) is read with one 16-byte and one 8-byte load instead of three
+#ifndef EOFA_WIDE_LINK_ROWS
+#define EOFA_WIDE_LINK_ROWS 1
+#endif
+
 template <>
 __device__ __forceinline__ void link_row<float>(const void* g, long long idx, int a, bool dag, cpx<float>* r) {
     const float2* b = (const float2*)g + idx * 10;
+    if (EOFA_WIDE_LINK_ROWS && !dag) {
+        const float4* b4 = (const float4*)g + idx * 5;
+        if (a == 0) {
+            const float4 t = __ldg(b4);
+            const float2 u = __ldg(b + 2);
+            r[0] = mk(t.x, t.y);
+            r[1] = mk(t.z, t.w);
+            r[2] = mk(u.x, u.y);
+        } else if (a == 1) {
+            const float2 u = __ldg(b + 3);
+            const float4 t = __ldg(b4 + 2);
+            r[0] = mk(u.x, u.y);
+            r[1] = mk(t.x, t.y);
+            r[2] = mk(t.z, t.w);
+        } else {
+            const float4 t = __ldg(b4 + 3);
+            const float2 u = __ldg(b + 8);
+            r[0] = mk(t.x, t.y);
+            r[1] = mk(t.z, t.w);
+            r[2] = mk(u.x, u.y);
+        }
+        return;
+    }
 #pragma unroll
     for (int k = 0; k < 3; k++) {
         float2 t = __ldg(b + (dag ? 3 * k + a : 3 * a + k));

@@ -121,6 +121,7 @@ void Solve::setup(eofa_ctx* c, const eofa_solve_params& prm, const double* b_dev
     if (!is_finite(fnorm2)) throw eofa_error(EOFA_ENUMERIC, "right-hand side has NaN/Inf");
     trivial = fnorm2 == 0.0;
     done = trivial;
+    x_zero = false;
     if (trivial) return;
     if (P.use_x0) {
         launch_pack(ctx, P64, x_dev, x_e, x_o, st);
@@ -131,6 +132,7 @@ void Solve::setup(eofa_ctx* c, const eofa_solve_params& prm, const double* b_dev
     } else {
         blas_zero(ctx, P64, x_o, st);
     }
+    x_zero = !P.use_x0;
     // f^_o = G'^{-1} (f_o - D_oe G'^{-1} f_e)
     launch_op5(ctx, P64, Gi, f_e, nullptr, a_e, st);
     launch_hop(ctx, P64, 1, 0, a_e, a_o, st);
@@ -153,9 +155,14 @@ void Solve::setup(eofa_ctx* c, const eofa_solve_params& prm, const double* b_dev
 }
 
 bool Solve::start_cg(cudaStream_t st) {
-    // r64 = f^ - A x_o (FP64)
-    apply_A(ctx, Gi, P64, x_o, r64, a_e, nullptr, 0, st);
-    blas_axpby(ctx, P64, 1.0, fh, -1.0, r64, st);
+    // r64 = f^ - A x_o (FP64); with x_o = 0 it is f^ itself (two FP64 hops saved)
+    if (x_zero) {
+        blas_copy(ctx, P64, r64, P64, fh, st);
+    } else {
+        apply_A(ctx, Gi, P64, x_o, r64, a_e, nullptr, 0, st);
+        blas_axpby(ctx, P64, 1.0, fh, -1.0, r64, st);
+    }
+    x_zero = false;
     double rr = norm2_now(ctx, P64, r64, st);
     if (!is_finite(rr)) throw eofa_error(EOFA_ENUMERIC, "NaN/Inf in the residual");
     target = target_rel * fhn;

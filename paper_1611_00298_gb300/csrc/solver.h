@@ -23,6 +23,7 @@ struct Solve {
     double fnorm2, fhn, rmax, target_rel, target, true_rel;
     int it, ring, restarts;
     bool done, trivial;
+    bool x_zero;       // x_o is known to be zero (no initial guess, CG not yet started)
     eofa_solve_info inf;
 
     // b_dev, x_dev: canonical 5D device fields (x_dev holds x0 when P.use_x0)
