@@ -339,6 +339,23 @@ def workload_config(wl, what):
             "parallelism": "replicas (one independent lattice per GPU)"}
 
 
+def replica_seed(seed, rank):
+    """Each rank integrates its own independent lattice (replicas, no data-path collective)."""
+    return seed + 100 * rank
+
+
+def replica_totals(dist, elapsed, nbytes, device):
+    """Whole-job figures over the ranks: the slowest rank's time and the summed bytes."""
+    if dist is None:
+        return elapsed, nbytes
+    import torch
+    t = torch.tensor([elapsed], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    b = torch.tensor([nbytes], device=device, dtype=torch.float64)
+    dist.all_reduce(b)
+    return float(t.item()), float(b.item())
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -399,8 +416,8 @@ def main():
 
     prec = eofa.PREC_MIXED_F32 if args.precision == "f32" else eofa.PREC_MIXED_F16
     Ls = wl["Ls"]
-    U = inputs.gauge_field(wl["dims"], wl["eps"], wl["seed"] + 100 * rank)
-    phi_np = inputs.fermion4d(wl["dims"], wl["seed"] + 100 * rank)
+    U = inputs.gauge_field(wl["dims"], wl["eps"], replica_seed(wl["seed"], rank))
+    phi_np = inputs.fermion4d(wl["dims"], replica_seed(wl["seed"], rank))
     lat = eofa.Lattice(wl["dims"], Ls, bc_t=wl["bc"])
     lat.gauge_load(U)
     phi = torch.from_numpy(phi_np).cuda()
@@ -443,15 +460,7 @@ def main():
     # algorithmic bytes counted per launch by the library (each spinor read /
     # written once, links once per 4D site, the axpy input when present)
     hop_bytes = sum(kind_bytes[p] for p in range(3))
-    t_max = elapsed
-    total_bytes = hop_bytes
-    if dist is not None:
-        t = torch.tensor([elapsed], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-        b = torch.tensor([hop_bytes], device="cuda", dtype=torch.float64)
-        dist.all_reduce(b)
-        total_bytes = float(b.item())
+    t_max, total_bytes = replica_totals(dist, elapsed, hop_bytes, "cuda")
     value = total_bytes / t_max / 1e9
 
     inner = 1 if prec == eofa.PREC_MIXED_F32 else 2
