@@ -842,6 +842,10 @@ int tuned_cfg(K1 k1, KB kb, KP2 kp2, KP3 kp3, const eofa_ctx* ctx, const Geom& g
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     EOFA_CUDA(cudaStreamIsCapturing(st, &cs));
     if (cs != cudaStreamCaptureStatusNone || (long long)g.Vh * g.Ls < (1LL << 20)) return def;
+    // FP64 storage is bound by the FP64 pipe: every configuration was measured
+    // within 1% (22.8-22.9 ms at 24^3 x 64 x 24), while trying them all costs
+    // ~2 s of FP64 launches per context, so FP64 keeps the heuristic tile
+    if (P == P64) return def;
     std::vector<int> cands;
     for (int c : {ns0 / 2, ns0, ns0 * 2, ns0 * 4})
         if (direct_ok(c)) cands.push_back(c * 4 + 1);
