@@ -127,6 +127,13 @@ int eofa_hop_dev(eofa_ctx* ctx, int precision, int out_parity, int dagger,
  * Same buffers and layouts as eofa_hop_dev. */
 int eofa_schur_hop_dev(eofa_ctx* ctx, int precision, int out_parity, int dagger, int Ls, double alpha,
                        double M5, double mf, const void* in_dev, void* out_dev, void* stream);
+/* Device status of the context: waits for the stream, then returns
+ * EOFA_ETIMEOUT (and clears the flag) if a bounded wait inside a staged
+ * (bulk-copy) dslash launch on this context ran out since the last check,
+ * else EOFA_OK.  Such a launch leaves its output undefined but the context
+ * usable.  Solves check this flag themselves when they finish; callers of the
+ * asynchronous *_dev kernels above can check it here. */
+int eofa_check_device(eofa_ctx* ctx, void* stream);
 /* Pack a canonical FP64 5D field (device) into the two half-checkerboard
  * device-layout fields of the given precision, and back. */
 int eofa_pack_dev(eofa_ctx* ctx, int precision, const double* canon_dev, void* even_dev,

@@ -220,6 +220,16 @@ const char* eofa_last_error(const eofa_ctx* ctx) {
     return ctx->err.c_str();
 }
 
+int eofa_check_device(eofa_ctx* ctx, void* stream) {
+    if (!ctx) return EOFA_EINVAL;
+    try {
+        check_device_error(ctx, (cudaStream_t)stream);
+    } catch (const eofa_error& e) {
+        return fail(ctx, e.code, e.msg);
+    }
+    return EOFA_OK;
+}
+
 int eofa_gauge_load_dev(eofa_ctx* ctx, const double* U_dev, void* stream) {
     if (!ctx || !U_dev) return fail(ctx, EOFA_EINVAL, "null argument");
     cudaStream_t st = (cudaStream_t)stream;

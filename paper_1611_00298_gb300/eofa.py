@@ -33,6 +33,7 @@ EXPORTS = [
     "eofa_dwf_apply_noalloc", "eofa_schur_hop_dev", "eofa_pseudofermion_solutions_dev",
     "eofa_set_reliable_delta", "eofa_leapfrog_dev", "eofa_rational_inv_sqrt", "eofa_heatbath_dev",
     "eofa_gauge_action_dev", "eofa_gauge_force_dev", "eofa_hmc_trajectory_dev", "eofa_force_parts_dev",
+    "eofa_check_device",
 ]
 INT_LEAPFROG, INT_FG_PQPQP, INT_FG_QPQPQ = 0, 1, 2
 
@@ -126,6 +127,7 @@ def load_library(path: str = LIB_PATH):
                                                  ctypes.POINTER(SolveInfo), P]),
         "eofa_set_reliable_delta": (I, [P, D]),
         "eofa_gauge_action_dev": (I, [P, D, P, ctypes.POINTER(D), P]),
+        "eofa_check_device": (I, [P, P]),
         "eofa_force_parts_dev": (I, [P, I, D, D, D, D, I, D, P, P, P, ctypes.POINTER(SolveInfo), P]),
         "eofa_gauge_force_dev": (I, [P, D, P, P, I, P]),
         "eofa_hmc_trajectory_dev": (I, [P, ctypes.POINTER(MDParams), P, P, P, ctypes.POINTER(MDInfo), P]),
@@ -411,6 +413,10 @@ class Lattice:
                                            info, _stream())
         self._check(rc, "force_parts_dev")
         return [info[0].as_dict(), info[1].as_dict()]
+
+    def check_device(self):
+        """Raise EOFAError (ETIMEOUT) if a staged dslash launch's bounded wait ran out since the last check."""
+        self._check(self.lib.eofa_check_device(self.ctx, _stream()), "check_device")
 
     def gauge_action_dev(self, beta, U=None):
         """Wilson plaquette action of U (device canonical) or of the context's links."""

@@ -99,3 +99,9 @@ def test_rational_inv_sqrt_error_shrinks_with_poles(libpath):
     errs = [eofa.rational_inv_sqrt(n, 1e-3, 10.0)[3] for n in (2, 4, 8, 16)]
     assert all(errs[i + 1] < 0.1 * errs[i] for i in range(3))
     assert eofa.rational_inv_sqrt(16, 1e-3, 10.0)[3] < 1e-10
+
+
+def test_check_device_rejects_null_context(libpath):
+    from paper_1611_00298_gb300 import eofa
+    lib = eofa.load_library(libpath)
+    assert lib.eofa_check_device(None, None) == eofa.EINVAL

@@ -212,4 +212,5 @@ def test_forced_dslash_configurations(eofa, cfg, monkeypatch):
             lat.unpack_dev(prec, out, zero, res)
             torch.cuda.synchronize()
             assert _rel(res.cpu().numpy(), ref) < tol, (cfg, prec, schur)
+    lat.check_device()  # no bounded wait of a staged launch ran out
     lat.close()
