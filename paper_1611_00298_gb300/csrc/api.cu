@@ -164,6 +164,11 @@ int eofa_create(eofa_ctx** out, const int dims[4], int Ls, int bc_t, int flags) 
     ctx->prof = nullptr;
     ctx->tuned = new std::map<long long, int>();
     ctx->forced_cfg = 0;
+    // test hook for the bounded waits of the staged dslash: its producer issues
+    // nothing, so the consumers' first wait runs out (about 1 s) and the launch
+    // reports EOFA_ETIMEOUT through the device error word
+    ctx->test_stall = 0;
+    if (const char* env = getenv("EOFA_TEST_STALL")) ctx->test_stall = atoi(env) > 0 ? atoi(env) : 0;
     if (const char* env = getenv("EOFA_DSLASH_CONFIG")) {
         // "NS,SPT" selects the direct kernel, "NS,SPT,D" the staged one with ring
         // depth D, "NS,SPT,-K" the pipelined one with K slots per thread

@@ -201,7 +201,7 @@ struct Ring {
 template <int P, int DAG, int LS, bool HASOP>
 __global__ void __launch_bounds__(BULK_MAX_THREADS, 2) dslash_bulk_kernel(
     Geom g, int par, const void* __restrict__ in, void* out, const void* __restrict__ gauge, Op5 op, const void* y,
-    double a_out, double b_in, double* red, int slot, int NS, int D, int* err) {
+    double a_out, double b_in, double* red, int slot, int NS, int D, int* err, int stall) {
     typedef typename Field<P>::R R;
     extern __shared__ __align__(128) unsigned char smraw[];
     const int Ls = LS > 0 ? LS : g.Ls;
@@ -237,7 +237,7 @@ __global__ void __launch_bounds__(BULK_MAX_THREADS, 2) dslash_bulk_kernel(
         const unsigned char* gb = static_cast<const unsigned char*>(gauge);
         Ring rg{0, 0, D}, after_last{0, 0, D};
         int issued = 0;
-        bool ok = true;
+        bool ok = !stall;  // stall (test hook): issue nothing, so the consumers' waits run out
         int e[8], en[8];
         int tile = blockIdx.x;
         if (tile < ntiles) {

@@ -798,7 +798,12 @@ void launch_bulk(K k, const eofa_ctx* ctx, const Geom& g, int NS, int D, bool ha
         EOFA_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, pl.total_b));
     unsigned grid = grid_size(k, threads, pl.total_b, ntiles, ctx->sms);
     int* err = reinterpret_cast<int*>(ctx->red + RED_ERRWORD);
-    k<<<grid, threads, pl.total_b, st>>>(g, par, in, out, gauge, op, y, a_out, b_in, red, slot, NS, D, err);
+    int stall = 0;
+    if (ctx->test_stall > 0) {
+        ctx->test_stall--;
+        stall = 1;
+    }
+    k<<<grid, threads, pl.total_b, st>>>(g, par, in, out, gauge, op, y, a_out, b_in, red, slot, NS, D, err, stall);
 }
 
 template <int P, typename KP2, typename KP3>

@@ -124,6 +124,7 @@ struct eofa_ctx {
     std::map<std::string, size_t> buf_sizes;
     Prof* prof;
     std::map<long long, int>* tuned;  // autotuned dslash configuration (NS * 4 + SPT), by kernel key
+    mutable int test_stall;           // EOFA_TEST_STALL=n: the next n staged dslash launches let a wait run out
     int forced_cfg;                   // EOFA_DSLASH_CONFIG="NS,SPT" at context creation (0: autotune)
     double rel_delta;  // reliable-update threshold of the solves inside action / force / MD
 };

@@ -214,3 +214,41 @@ def test_forced_dslash_configurations(eofa, cfg, monkeypatch):
             assert _rel(res.cpu().numpy(), ref) < tol, (cfg, prec, schur)
     lat.check_device()  # no bounded wait of a staged launch ran out
     lat.close()
+
+
+def test_staged_wait_runs_out_and_reports(eofa, monkeypatch):
+    """Failure detection of the staged dslash without a GPU fault: with the
+    EOFA_TEST_STALL hook its producer warp issues no copy, so the consumers'
+    first bounded wait runs out (about a second), the launch finishes, and the
+    host reads EOFA_ETIMEOUT; the context stays usable and the next launch is
+    correct."""
+    import torch
+    monkeypatch.setenv("EOFA_DSLASH_CONFIG", "4,1,2")
+    monkeypatch.setenv("EOFA_TEST_STALL", "1")
+    dims, Ls, bc = (4, 4, 2, 6), 24, -1
+    lat, U = _setup(eofa, dims, Ls, bc)
+    psi = inputs.fermion5d(dims, Ls, 7)
+    X, Y, Z, T = dims
+    t, z, y, x = np.meshgrid(*[np.arange(n) for n in (T, Z, Y, X)], indexing="ij")
+    par = (x + y + z + t) % 2
+    src = psi * (par == 1)[None, :, :, :, :, None, None]
+    ref = dwf.wilson_hop(U, src, bc) * (par == 0)[None, :, :, :, :, None, None]
+    prec = 1
+    nb = lat.field_bytes(prec)
+    ev = torch.empty(nb, dtype=torch.uint8, device="cuda")
+    od, out = torch.empty_like(ev), torch.empty_like(ev)
+    zero = torch.zeros_like(ev)
+    lat.pack_dev(prec, torch.from_numpy(src.copy()).cuda(), ev, od)
+    lat.pack_dev(prec, torch.zeros(lat.shape5, dtype=torch.complex128, device="cuda"), zero, zero)
+    lat.hop_dev(prec, 0, 0, od, out)  # stalls
+    with pytest.raises(eofa.EOFAError) as ei:
+        lat.check_device()
+    assert ei.value.code == eofa.ETIMEOUT
+    lat.check_device()  # the flag was cleared
+    lat.hop_dev(prec, 0, 0, od, out)
+    res = torch.empty(lat.shape5, dtype=torch.complex128, device="cuda")
+    lat.unpack_dev(prec, out, zero, res)
+    lat.check_device()
+    torch.cuda.synchronize()
+    assert _rel(res.cpu().numpy(), ref) < 2e-6
+    lat.close()
