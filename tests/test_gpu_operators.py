@@ -252,3 +252,46 @@ def test_staged_wait_runs_out_and_reports(eofa, monkeypatch):
     torch.cuda.synchronize()
     assert _rel(res.cpu().numpy(), ref) < 2e-6
     lat.close()
+
+
+@pytest.mark.parametrize("cfg", ["4,1,2", "3,1,-2", "4,1,-3"])
+@pytest.mark.parametrize("Ls", [5, 8, 12, 16])
+def test_variant_kernels_every_ls(eofa, cfg, Ls, monkeypatch):
+    """The staged and pipelined dslash variants at the other compile-time Ls
+    extents (8, 12, 16) and the generic one (Ls = 5), both dagger and both
+    output parities, against the oracle hop and dense 5D blocks.  Shapes a
+    variant cannot take (FP16 staging needs Ls % 4 == 0) fall back to the
+    direct kernel and must still agree."""
+    import torch
+    monkeypatch.setenv("EOFA_DSLASH_CONFIG", cfg)
+    dims, alpha, M5, mf, bc = (4, 2, 2, 6), 2.0, 1.8, 0.1, -1
+    lat, U = _setup(eofa, dims, Ls, bc)
+    psi = inputs.fermion5d(dims, Ls, 8)
+    X, Y, Z, T = dims
+    t, z, y, x = np.meshgrid(*[np.arange(n) for n in (T, Z, Y, X)], indexing="ij")
+    par = (x + y + z + t) % 2
+    Gp, Gm = _ginv_blocks(Ls, alpha, M5, mf)
+    for prec, tol in ((0, 1e-12), (1, 2e-6), (2, 3e-3)):
+        nb = lat.field_bytes(prec)
+        for out_par in (0, 1):
+            for dag in (0, 1):
+                src = psi * (par == 1 - out_par)[None, :, :, :, :, None, None]
+                hop = dwf.wilson_hop(U, src, bc, dagger=bool(dag))
+                ref = dwf.apply_s(Gp.T, Gm.T, hop) if dag else dwf.apply_s(Gp, Gm, hop)
+                ref = ref * (par == out_par)[None, :, :, :, :, None, None]
+                dev = torch.from_numpy(src.copy()).cuda()
+                ev = torch.empty(nb, dtype=torch.uint8, device="cuda")
+                od, out = torch.empty_like(ev), torch.empty_like(ev)
+                zero = torch.zeros_like(ev)
+                lat.pack_dev(prec, dev, ev, od)
+                lat.pack_dev(prec, torch.zeros_like(dev), zero, zero)
+                lat.schur_hop_dev(prec, out_par, dag, od if out_par == 0 else ev, out, alpha, M5, mf)
+                res = torch.empty_like(dev)
+                if out_par == 0:
+                    lat.unpack_dev(prec, out, zero, res)
+                else:
+                    lat.unpack_dev(prec, zero, out, res)
+                torch.cuda.synchronize()
+                assert _rel(res.cpu().numpy(), ref) < tol, (cfg, Ls, prec, out_par, dag)
+    lat.check_device()
+    lat.close()
