@@ -174,3 +174,28 @@ def test_split_lr_trajectory_matches_oracle(eofa, order, outer):
     assert np.abs(Pd.cpu().numpy() - P1).max() < 1e-9
     assert info["dH"] == pytest.approx(dH, abs=1e-8)
     lat.close()
+
+
+def test_mixed_precision_trajectory_matches_fp64(eofa):
+    """The trajectory with mixed FP32 solves (FP64 reliable updates, true
+    residual 1e-11) ends where the all-FP64 one does, to the solver tolerance."""
+    import torch
+    dims, Ls = (4, 4, 4, 4), 8
+    U = inputs.gauge_field(dims, 0.3, 31)
+    P = inputs.momenta(dims, 32)
+    phi = inputs.fermion4d(dims, 33)
+    kw = dict(alpha=ALPHA, M5=M5, m1=M1, m2=M2, tol=1e-11, beta=BETA, integrator=eofa.INT_FG_QPQPQ, tau=0.5,
+              nsteps=2, n_inner=2)
+    lat = eofa.Lattice(dims, Ls)
+    ends = []
+    for prec in (eofa.PREC_F64, eofa.PREC_MIXED_F32):
+        lat.gauge_load(U)
+        Pd = _dev(P)
+        Ud = torch.empty_like(Pd)
+        info = lat.hmc_trajectory_dev(Pd, _dev(phi), Ud, precision=prec, **kw)
+        ends.append((Ud.cpu().numpy(), Pd.cpu().numpy(), info["dH"]))
+    (U64, P64, dH64), (U32, P32, dH32) = ends
+    assert np.abs(U32 - U64).max() < 1e-8
+    assert np.abs(P32 - P64).max() < 1e-7
+    assert abs(dH32 - dH64) < 1e-6 * max(1.0, abs(dH64))
+    lat.close()
