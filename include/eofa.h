@@ -5,7 +5,9 @@
  * Paper: D. Murphy, "Domain Wall Fermion Simulations with the Exact
  * One-Flavor Algorithm", Lattice 2016.  Equation numbers below are the
  * paper's: Eq. (3) D_DWF = D_EOFA * D-tilde, Eq. (5) the EOFA action,
- * Eq. (7) the pseudofermion force, Eq. (8) the EOFA linear systems.
+ * Eq. (6) the heatbath, Eq. (7) the pseudofermion force, Eq. (8) the EOFA
+ * linear systems; Sec. 5 the HMC trajectory (gauge action, force-gradient
+ * integrators).
  *
  * Conventions shared by every call
  * --------------------------------
@@ -45,7 +47,7 @@ extern "C" {
 #define EOFA_ENOMEM (-2)    /* device allocation failed */
 #define EOFA_ENOTCONV (-3)  /* solver hit maxiter; info still filled */
 #define EOFA_ENUMERIC (-4)  /* NaN or Inf met */
-#define EOFA_ETIMEOUT (-5)  /* device watchdog expired */
+#define EOFA_ETIMEOUT (-5)  /* a bounded device wait ran out (see eofa_check_device) */
 #define EOFA_EDEVICE (-6)   /* CUDA error; message has the CUDA string */
 
 /* storage / arithmetic of the solver's inner iteration */
