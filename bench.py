@@ -273,6 +273,54 @@ def hmc_bench(args):
     return 0
 
 
+def hmc_chain_bench(args):
+    """HMC Markov chain: pure-gauge thermalisation, then EOFA trajectories with heatbath refresh
+    and Metropolis; acceptance and <exp(-dH)> (Sec. 3, Sec. 5; Table 3 analogue)."""
+    import numpy as np
+    import torch
+
+    from paper_1611_00298_gb300 import build, eofa, inputs
+    if not os.path.exists(eofa.LIB_PATH):
+        build.build()
+    dims, Ls, beta = (8, 8, 8, 8), 8, 5.7
+    n_therm, n_traj = 60, args.chain_traj
+    U = inputs.gauge_field(dims, 0.5, 41)
+    lat = eofa.Lattice(dims, Ls, bc_t=-1)
+    lat.gauge_load(U)
+    Pth = torch.from_numpy(np.stack([inputs.momenta(dims, 42, stream=10 + k) for k in range(n_therm)])).cuda()
+    uth = inputs.uniform(inputs.stream_key(42, 1), n_therm)
+    t0 = time.perf_counter()
+    th = lat.hmc_dev(Pth, None, uth, beta=beta, integrator=eofa.INT_FG_QPQPQ, nsteps=4, tau=1.0)
+    t_therm = time.perf_counter() - t0
+    del Pth
+    a0, al, be, err = eofa.rational_inv_sqrt(12, 1e-3, 20.0)
+    Ps = torch.from_numpy(np.stack([inputs.momenta(dims, 43, stream=10 + k) for k in range(n_traj)])).cuda()
+    etas = torch.from_numpy(np.stack([inputs.fermion4d(dims, 44, stream=10 + k) for k in range(n_traj)])).cuda()
+    us = inputs.uniform(inputs.stream_key(45, 1), n_traj)
+    kw = dict(alpha=2.0, M5=1.8, m1=0.04, m2=1.0, precision=eofa.PREC_MIXED_F32, tol=1e-10, beta=beta,
+              integrator=eofa.INT_FG_QPQPQ, nsteps=4, tau=1.0, n_inner=2)
+    t0 = time.perf_counter()
+    info = lat.hmc_dev(Ps, etas, us, rational=(a0, al, be), **kw)
+    t_chain = time.perf_counter() - t0
+    e = np.array([i["exp_minus_dH"] for i in info])
+    dH = np.array([i["dH"] for i in info])
+    out = {"hmc_chain": True, "lattice": "x".join(map(str, dims)), "Ls": Ls, "beta": beta, "m1": 0.04, "m2": 1.0,
+           "alpha": 2.0, "integrator": "nested force-gradient QPQPQ (4 EOFA steps, 2 gauge steps each), tau = 1",
+           "heatbath": f"12-pole Zolotarev x^-1/2 on [1e-3, 20], max rel err {err:.1e}",
+           "thermalisation": {"trajectories": n_therm, "acceptance": float(np.mean([i["accepted"] for i in th])),
+                              "plaquette_end": th[-1]["plaquette"], "seconds": round(t_therm, 2)},
+           "trajectories": n_traj, "acceptance": float(np.mean([i["accepted"] for i in info])),
+           "exp_minus_dH_mean": float(e.mean()), "exp_minus_dH_err": float(e.std(ddof=1) / np.sqrt(len(e))),
+           "dH_mean": float(dH.mean()), "dH_rms": float(np.sqrt(np.mean(dH ** 2))),
+           "plaquette_mean": float(np.mean([i["plaquette"] for i in info])),
+           "S_start_over_eta2": float(np.mean([i["S_eofa_start"] / i["eta_norm2"] for i in info])),
+           "seconds_per_trajectory": round(t_chain / n_traj, 3),
+           "solver_iters_per_trajectory": float(np.mean([i["solver_iters"] for i in info]))}
+    print(json.dumps(out), flush=True)
+    lat.close()
+    return 0
+
+
 def batched(args):
     """Three lattices x (3 mass pairs x {L, R} EOFA systems + 2 D_DWF systems) = 24 solves."""
     import numpy as np
@@ -378,6 +426,10 @@ def main():
     ap.add_argument("--hmc", action="store_true",
                     help="one nested force-gradient QPQPQ trajectory at 16^3x32, Ls=12 (EOFA + Wilson gauge), "
                          "one level and split L/R")
+    ap.add_argument("--hmc-chain", action="store_true",
+                    help="HMC chain at 8^4, Ls=8: pure-gauge thermalisation, then EOFA trajectories with heatbath "
+                         "refresh and Metropolis; acceptance and <exp(-dH)>")
+    ap.add_argument("--chain-traj", type=int, default=24)
     ap.add_argument("--batched", action="store_true",
                     help="24 solves on three lattices (8^4x8, 12^4x12, 16^3x32x16): one batched, graph-captured "
                          "mixed-precision call vs sequential FP64 solves")
@@ -393,6 +445,8 @@ def main():
         return heatbath_bench(args)
     if args.hmc:
         return hmc_bench(args)
+    if args.hmc_chain:
+        return hmc_chain_bench(args)
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -294,6 +294,36 @@ typedef struct {
 int eofa_hmc_trajectory_dev(eofa_ctx* ctx, const eofa_md_params* p, const double* phi_dev, double* P_dev,
                             double* U_dev, eofa_md_info* info, void* stream);
 
+/* HMC Markov chain (Sec. 3 and Sec. 5): ntraj trajectories, each
+ *   1. pseudofermion refresh phi = f(M_EOFA) eta_k by the heatbath of
+ *      Eq. (6) (eofa_heatbath_dev with alpha0, alphas, betas; forecasting
+ *      on), skipped when npoles = 0 (pure gauge chain, md->beta > 0);
+ *   2. momenta P_k and one trajectory of eofa_hmc_trajectory_dev (md) from
+ *      the current links;
+ *   3. Metropolis: accept when u[k] < exp(-dH) (a NaN dH is rejected); a
+ *      rejected trajectory restores the links it started from.
+ * The context's links are the chain's state: they start as loaded and end
+ * at the last accepted configuration (copied to U_dev, canonical, if not
+ * NULL).  All random numbers are inputs: P_dev holds ntraj momentum fields
+ * (each 4 V traceless Hermitian 3x3, canonical, device), eta_dev ntraj 4D
+ * Gaussian fields (device; may be NULL when npoles = 0), u ntraj uniforms
+ * in [0, 1) (host).  info[k] gets trajectory k's record.  EOFA_EINVAL for
+ * bad arguments; a failed solve or trajectory stops the chain with its
+ * status (info holds the records of the trajectories before it). */
+typedef struct {
+    double H0, dH;        /* H at the trajectory's start, H(end) - H(start) */
+    double exp_minus_dH;  /* exp(-dH) (its chain average estimates <exp(-dH)> = 1) */
+    int accepted;         /* 1 if the Metropolis step accepted the trajectory */
+    double plaquette;     /* average Re tr U_p / 3 after the accept/reject step */
+    double S_eofa_start;  /* S_EOFA(phi) at the start: equals eta^+ eta up to the rational error */
+    double eta_norm2;     /* eta^+ eta (0 when npoles = 0) */
+    int solver_iters;     /* CG iterations of the heatbath and the trajectory */
+    double seconds;       /* wall time of the trajectory, heatbath included */
+} eofa_hmc_traj_info;
+int eofa_hmc_dev(eofa_ctx* ctx, const eofa_md_params* md, int ntraj, double alpha0, int npoles,
+                 const double* alphas, const double* betas, const double* P_dev, const double* eta_dev,
+                 const double* u, double* U_dev, eofa_hmc_traj_info* info, void* stream);
+
 /* Molecular dynamics link update U <- exp(i eps P) U on the device gauge
  * field of the context and on the canonical copy U_dev (if not NULL);
  * P: 4 V traceless Hermitian 3x3, canonical, device. */
@@ -314,15 +344,19 @@ int eofa_solve_batched(eofa_ctx* const* ctxs, int n, const eofa_solve_params* pa
  * allocator up front (a fresh cudaMalloc would fail or fragment the pool)
  * and latency-critical loops that cannot afford cudaMalloc's implicit device
  * synchronisation.
- *   - Temporaries live in one 16 MiB static device array that every GPU
- *     which loads libeofa keeps until the process exits.  Lattices needing
- *     more (384 V Ls bytes > 16 MiB, e.g. anything above 8^4 x 8) are
- *     rejected with EOFA_EINVAL and a message giving both sizes.
+ *   - Temporaries live in one 16 MiB static device array per device.  It
+ *     is taken, and its device address resolved, when the first context on
+ *     that device is created (eofa_create, which allocates anyway), and kept
+ *     until the process exits; the calls themselves load no module and do
+ *     no set-up.
+ *   - Size limit: the four temporaries are FP64 half-checkerboard fields
+ *     of 96 V Ls bytes each, each rounded up to a multiple of 256 bytes, so
+ *     the lattice must satisfy 4 * round256(96 V Ls) <= 16 MiB, about
+ *     384 V Ls bytes (8^4 x 8, 8^4 x 10 and 4^4 x 64 fit; 8^4 x 16 does
+ *     not).  Larger lattices are rejected with EOFA_EINVAL and a message
+ *     giving both sizes.
  *   - The context must already exist with its gauge field loaded (those
  *     calls allocate) and its device must be current (else EOFA_EINVAL).
- *   - The first call on each device looks up the array's device address
- *     with cudaGetSymbolAddress; make that first call before any stream
- *     capture.
  *   - Every call uses the same array: calls that overlap on the GPU (other
  *     streams, threads or contexts at the same time) race and corrupt each
  *     other's results.  Each call writes every temporary before reading it,

@@ -233,3 +233,29 @@ def wilson_hop_at(U, psi, site, s, bc_t, dagger=False):
         vb = pb * (psi[s][bwd] @ np.conj(Ub))          # U_mu(x - mu)^+ psi(x - mu)
         out -= 0.5 * ((one - sgn * GAMMA[mu]) @ vf + (one + sgn * GAMMA[mu]) @ vb)
     return out
+
+
+def _site_slab(psi, site):
+    """psi at one 4D site for every s, keeping singleton lattice axes: (Ls, 1, 1, 1, 1, 4, 3)."""
+    t, z, y, x = site
+    return psi[:, t:t + 1, z:z + 1, y:y + 1, x:x + 1]
+
+
+def wilson_at(U, psi, M5, site, bc_t):
+    """D_w psi at one 4D site for every s: (4 - M5) psi + the hop (Sec. 2), shape (Ls, 4, 3)."""
+    Ls = psi.shape[0]
+    t, z, y, x = site
+    return np.stack([(4.0 - M5) * psi[s, t, z, y, x] + wilson_hop_at(U, psi, site, s, bc_t) for s in range(Ls)])
+
+
+def dwf_at(U, psi, alpha, M5, mf, bc_t, site, Lpsi=None):
+    """(D_DWF psi) at one 4D site for every s, the first line of Eq. (3) evaluated
+    from that site's neighbours only; shape (Ls, 4, 3).  Lpsi = L psi on the
+    whole lattice may be passed in (it is site-local in 4D and reused across
+    sites)."""
+    c, d = coefficients(alpha)
+    if Lpsi is None:
+        Lpsi = L_apply(psi, mf)
+    t, z, y, x = site
+    return ((c + d) * wilson_at(U, psi, M5, site, bc_t) + psi[:, t, z, y, x]
+            + (c - d) * wilson_at(U, Lpsi, M5, site, bc_t) - Lpsi[:, t, z, y, x])

@@ -104,6 +104,28 @@ def system_apply(U, psi, alpha, M5, m1, m2, which, a, bc_t):
     return out
 
 
+def system_apply_at(U, psi, alpha, M5, m1, m2, which, a, bc_t, site):
+    """(H(m) + a Delta_chi P_chi) psi at one 4D site for every s, shape (Ls, 4, 3).
+
+    The same definition as system_apply: H = gamma_5 R_5 (D_w + D^perp) with
+    D_w evaluated from the site's eight neighbours (dwf.wilson_at) and the
+    5D-local D^perp and Delta terms, which act on the s index of the site
+    alone; for checking solutions on lattices too large for whole-field numpy.
+    """
+    Ls = psi.shape[0]
+    m = m1 if which == "L" else m2
+    slab = dwf._site_slab(psi, site)
+    Pp, Pm = dwf.dperp_matrices(Ls, alpha, m)
+    deo = dwf.wilson_at(U, psi, M5, site, bc_t) + dwf.apply_s(Pp, Pm, slab)[:, 0, 0, 0, 0]
+    out = dwf.gamma5(dwf.R5(deo))
+    if a != 0.0:
+        Dp, Dm = delta_matrices(Ls, alpha, m1, m2)
+        zero = np.zeros((Ls, Ls))
+        term = dwf.apply_s(zero, Dm, slab) if which == "L" else dwf.apply_s(Dp, zero, slab)
+        out = out + a * term[:, 0, 0, 0, 0]
+    return out
+
+
 def system_solve(U, rhs, alpha, M5, m1, m2, which, a, bc_t, tol=1e-12, maxiter=20000):
     """Solve (H(m) + a Delta P) psi = rhs (Hermitian system) by CGNR."""
     A = lambda v: system_apply(U, v, alpha, M5, m1, m2, which, a, bc_t)  # noqa: E731

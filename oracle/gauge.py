@@ -205,3 +205,42 @@ def split_lr_trajectory(U, P, beta, fermion, tau, nsteps, n_middle, n_inner, sch
         levels.append((lambda U_: force(U_, beta), n_inner))
     forces = Forces(beta, fermion)
     return trajectory_levels(U, P, levels, forces.energy, tau, scheme)
+
+
+# ---------------------------------------------------------------- HMC chain (Sec. 3, Sec. 5)
+
+def metropolis(dH, u):
+    """The HMC accept test: accept with probability min(1, exp(-dH)), decided
+    by a uniform u in [0, 1): accept when u < exp(-dH).  A NaN dH is rejected."""
+    return bool(np.isfinite(dH) and u < np.exp(-dH))
+
+
+def hmc_chain(U, Ps, us, beta, tau, nsteps, scheme="qpqpq", n_inner=0, fermion=None, etas=None, rational=None):
+    """HMC Markov chain of len(us) trajectories.
+
+    Trajectory k: when ``fermion`` is given (dict(Ls, alpha, M5, m1, m2, bc_t,
+    tol)), a fresh pseudofermion phi = f(M_EOFA) eta_k from the heatbath of
+    Eq. (6) with f(x) = alpha0 + sum_l alphas[l] / (x + betas[l]) (rational =
+    (alpha0, alphas, betas)); the MD trajectory of H = sum tr P^2 + S_g +
+    S_EOFA(phi) from momenta Ps[k] (``trajectory``); the Metropolis step with
+    us[k].  A rejected trajectory keeps the links it started from.  Returns
+    (U, records) with records[k] = (dH, accepted, S_EOFA(phi) at the start).
+    """
+    recs = []
+    for k, (P, u) in enumerate(zip(Ps, us)):
+        f = None
+        S_start = 0.0
+        if fermion is not None:
+            a0, al, be = rational
+            fp = fermion
+            phi = oeofa.heatbath(U, etas[k], fp["Ls"], fp["alpha"], fp["M5"], fp["m1"], fp["m2"], fp["bc_t"], a0,
+                                 al, be, fp["tol"])
+            f = dict(fermion, phi=phi)
+            S_start = oeofa.action(U, phi, fp["Ls"], fp["alpha"], fp["M5"], fp["m1"], fp["m2"], fp["bc_t"], fp["tol"])
+        forces = Forces(beta, f)
+        U1, _, dH = trajectory(U, P, forces, tau, nsteps, scheme, n_inner)
+        acc = metropolis(dH, u)
+        if acc:
+            U = U1
+        recs.append((dH, acc, S_start))
+    return U, recs

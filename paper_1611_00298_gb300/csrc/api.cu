@@ -196,6 +196,7 @@ int eofa_create(eofa_ctx** out, const int dims[4], int Ls, int bc_t, int flags) 
         ctx->red = (double*)ctx_buffer(ctx, "red", red_scratch_bytes());
         EOFA_CUDA(cudaMemset(ctx->red, 0, red_scratch_bytes()));
         EOFA_CUDA(cudaMallocHost((void**)&ctx->red_host, 64 * sizeof(double)));
+        noalloc_prepare(ctx->device);
     } catch (const eofa_error& e) {
         int code = e.code;
         eofa_destroy(ctx);

@@ -1,21 +1,246 @@
 // Batched solves: many independent systems of Eq. (8) (or D_DWF systems),
-// possibly on several lattices, iterated together.  The heatbath needs 2 N_p
-// such solves and the force 2 (Sec. 3.2, 3.3, 5.2); on small lattices each
-// alone leaves most of the GPU idle and is bound by launch latency.
+// possibly on several lattices.  The heatbath needs 2 N_p such solves and
+// the force 2 (Sec. 3.2, 3.3, 5.2); the mass pairs of several EOFA factors
+// add more.
 //
-// Every system keeps its own reduction scratch and device scalars, so the
-// iterations of all active systems can run concurrently: a chunk of 16 CG
-// iterations of every active system is captured once into a CUDA graph
-// (one stream per system, forked from and joined to an origin stream) and
-// replayed; between replays the host reads each system's residual, does
-// reliable updates and retires converged systems (which triggers a
-// re-capture for the smaller active set).
+// Systems on the same lattice and with the same inner precision form a
+// group (at most MR_MAX systems).  A group iterates its systems in lock
+// step with the multi-system kernels of mrhs.cuh: one launch per CG step
+// for all of them, each link row and neighbour index fetched once for the
+// whole group.  The CG loop of a group runs on the device: a CUDA graph
+// holds one WHILE conditional node whose body is K CG iterations of every
+// active system followed by a one-block decision kernel; the kernel reads
+// each system's |r|^2 and keeps the loop going until some system has
+// reached its inner target, needs an FP64 reliable update, diverges or
+// runs out of iterations.  Only then does the host look at the group: it
+// does the reliable updates and the true-residual checks of solver.cu,
+// retires converged systems (re-capturing the graph for the smaller set)
+// and relaunches.  Groups run concurrently on their own streams; the host
+// services whichever group's graph has finished.
+#include "mrhs.h"
 #include "solver.h"
 
 #include <chrono>
+#include <cmath>
+#include <map>
 #include <memory>
+#include <thread>
 
-#define BATCH_CHUNK 16
+// CG iterations per loop body; the residual ring of every batched system
+// has this length, so the ring slots and CG-scalar parities baked into the
+// body stay valid on every pass (the iteration counter of every system is a
+// multiple of MR_BODY whenever the graph starts)
+#define MR_BODY 8
+
+// control block of a group (doubles, device): per system the squared
+// threshold that sends it to the host, the squared divergence bound, the
+// iterations left; outputs: last |r|^2 per system and iterations run
+#define CTL_THR 0
+#define CTL_RMAX (CTL_THR + MR_MAX)
+#define CTL_LEFT (CTL_RMAX + MR_MAX)
+#define CTL_RR (CTL_LEFT + MR_MAX)
+#define CTL_ITERS (CTL_RR + MR_MAX)
+#define CTL_DOUBLES (CTL_ITERS + 8)
+
+namespace {
+
+__global__ void mr_decide_kernel(MRPtrs a, int nr, double* ctl, cudaGraphConditionalHandle h) {
+    __shared__ int stop;
+    if (threadIdx.x == 0) {
+        stop = 0;
+        ctl[CTL_ITERS] += (double)MR_BODY;
+    }
+    __syncthreads();
+    const int t = threadIdx.x;
+    if (t < nr) {
+        const double rr = a.red[t][SC_RRH + (MR_BODY - 1)];
+        ctl[CTL_RR + t] = rr;
+        const bool bad = !(rr == rr) || rr > 1e300;
+        if (bad || rr < ctl[CTL_THR + t] || rr > ctl[CTL_RMAX + t] || ctl[CTL_ITERS] >= ctl[CTL_LEFT + t])
+            atomicOr(&stop, 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) cudaGraphSetConditional(h, stop ? 0u : 1u);
+}
+
+void mr_dslash(const eofa_ctx* ctx, int prec, int par, int dag, const MRPtrs& a, const Op5* ops, int nr, bool hasop,
+               double a_out, double b_in, int slot, cudaStream_t st) {
+    if (prec == P64) mr_dslash_p64(ctx, par, dag, a, ops, nr, hasop, a_out, b_in, slot, st);
+    else if (prec == P32) mr_dslash_p32(ctx, par, dag, a, ops, nr, hasop, a_out, b_in, slot, st);
+    else mr_dslash_p16(ctx, par, dag, a, ops, nr, hasop, a_out, b_in, slot, st);
+}
+
+void mr_local5(const eofa_ctx* ctx, int prec, const MRPtrs& a, const Op5* ops, int nr, int it, int slot,
+               cudaStream_t st) {
+    if (prec == P64) mr_local5_p64(ctx, a, ops, nr, it, slot, st);
+    else if (prec == P32) mr_local5_p32(ctx, a, ops, nr, it, slot, st);
+    else mr_local5_p16(ctx, a, ops, nr, it, slot, st);
+}
+
+void mr_xp(const eofa_ctx* ctx, int prec, const MRPtrs& a, int nr, int it, cudaStream_t st) {
+    if (prec == P64) mr_xp_p64(ctx, a, nr, it, st);
+    else if (prec == P32) mr_xp_p32(ctx, a, nr, it, st);
+    else mr_xp_p16(ctx, a, nr, it, st);
+}
+
+struct Group {
+    eofa_ctx* ctx = nullptr;
+    int prec = 0;
+    std::vector<int> members;   // system indices
+    std::vector<int> captured;  // active systems baked into the graph
+    cudaStream_t st = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaEvent_t done = nullptr;
+    Op5* ops = nullptr;          // device: [Gi x MR_MAX][GiT x MR_MAX] of the captured set
+    double* ctl = nullptr;       // device control block
+    double* ctl_host = nullptr;  // pinned mirror
+    bool running = false;
+    bool finished = false;
+};
+
+// One lock-step CG iteration (it) of the captured systems: the six fused
+// launches of Solve::enqueue, each for all systems at once.
+void enqueue_group_iteration(Group& g, std::vector<Solve>& sv, int it, cudaStream_t st) {
+    const int n = (int)g.captured.size();
+    MRPtrs k1 = {}, k2 = {}, k3 = {}, k4 = {}, k5 = {}, k6 = {};
+    for (int a = 0; a < n; a++) {
+        Solve& s = sv[g.captured[a]];
+        k1.in[a] = s.p;  k1.out[a] = s.te; k1.red[a] = s.red;
+        k2.in[a] = s.te; k2.out[a] = s.q;  k2.y[a] = s.p;   k2.red[a] = s.red;
+        k3.out2[a] = s.r; k3.y[a] = s.q;   k3.out[a] = s.to; k3.red[a] = s.red;
+        k4.in[a] = s.to; k4.out[a] = s.te; k4.red[a] = s.red;
+        k5.in[a] = s.te; k5.out[a] = s.s;  k5.y[a] = s.r;   k5.red[a] = s.red;
+        k6.out2[a] = s.x; k6.out[a] = s.p; k6.in[a] = s.s;  k6.red[a] = s.red;
+    }
+    const Op5* Gi = g.ops;
+    const Op5* GiT = g.ops + MR_MAX;
+    // q = A p: te = G'^-1 D_eo p; q = p - G'^-1 D_oe te, |q|^2 -> delta
+    mr_dslash(g.ctx, g.prec, 0, 0, k1, Gi, n, true, 1.0, 0.0, -1, st);
+    mr_dslash(g.ctx, g.prec, 1, 0, k2, Gi, n, true, -1.0, 1.0, SC_DELTA, st);
+    // r -= alpha q, |r|^2 -> ring; to = G'^-T r
+    mr_local5(g.ctx, g.prec, k3, GiT, n, it, SC_RRH + (it % MR_BODY), st);
+    // s = A^+ r: te = G'^-T D^+_eo to; s = r - D^+_oe te, |s|^2 -> gamma (next parity)
+    mr_dslash(g.ctx, g.prec, 0, 1, k4, GiT, n, true, 1.0, 0.0, -1, st);
+    mr_dslash(g.ctx, g.prec, 1, 1, k5, GiT, n, false, -1.0, 1.0, SC_GAMMA + ((it + 1) & 1), st);
+    // x += alpha p; p = s + beta p
+    mr_xp(g.ctx, g.prec, k6, n, it, st);
+}
+
+void destroy_graph(Group& g) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (g.graph) cudaGraphDestroy(g.graph);
+    g.exec = nullptr;
+    g.graph = nullptr;
+    g.captured.clear();
+}
+
+// Graph of the group's device loop for the active set: WHILE(cond) { MR_BODY
+// iterations; decide }.
+void build_graph(Group& g, std::vector<Solve>& sv, const std::vector<int>& active) {
+    destroy_graph(g);
+    g.captured = active;
+    const int n = (int)active.size();
+    std::vector<Op5> h(2 * MR_MAX);
+    for (int a = 0; a < n; a++) {
+        h[a] = op_finalize(sv[active[a]].Gi, g.ctx->Ls);
+        h[MR_MAX + a] = op_finalize(sv[active[a]].GiT, g.ctx->Ls);
+    }
+    EOFA_CUDA(cudaMemcpyAsync(g.ops, h.data(), h.size() * sizeof(Op5), cudaMemcpyHostToDevice, g.st));
+    EOFA_CUDA(cudaStreamSynchronize(g.st));
+    EOFA_CUDA(cudaGraphCreate(&g.graph, 0));
+    cudaGraphConditionalHandle handle;
+    EOFA_CUDA(cudaGraphConditionalHandleCreate(&handle, g.graph, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = handle;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    EOFA_CUDA(cudaGraphAddNode(&node, g.graph, nullptr, nullptr, 0, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    const bool prof_on = g.ctx->prof && g.ctx->prof->on;
+    if (g.ctx->prof) g.ctx->prof->on = false;  // no event records inside a conditional body
+    try {
+        EOFA_CUDA(cudaStreamBeginCaptureToGraph(g.st, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+        for (int it = 0; it < MR_BODY; it++) enqueue_group_iteration(g, sv, it, g.st);
+        MRPtrs d = {};
+        for (int a = 0; a < n; a++) d.red[a] = sv[active[a]].red;
+        mr_decide_kernel<<<1, 32, 0, g.st>>>(d, n, g.ctl, handle);
+        EOFA_LAUNCHED();
+        cudaGraph_t captured = nullptr;
+        EOFA_CUDA(cudaStreamEndCapture(g.st, &captured));
+    } catch (...) {
+        if (g.ctx->prof) g.ctx->prof->on = prof_on;
+        cudaStreamCaptureStatus cs;
+        if (cudaStreamIsCapturing(g.st, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) {
+            cudaGraph_t gg = nullptr;
+            cudaStreamEndCapture(g.st, &gg);
+        }
+        cudaGetLastError();
+        throw;
+    }
+    if (g.ctx->prof) g.ctx->prof->on = prof_on;
+    EOFA_CUDA(cudaGraphInstantiate(&g.exec, g.graph, 0));
+}
+
+// Retire, restart or keep the group's systems after a host check; launch the
+// device loop for the ones still iterating.  Returns false when every
+// system of the group has finished.
+bool service_group(Group& g, std::vector<Solve>& sv, std::vector<bool>& finished, std::vector<double*>& xdev) {
+    std::vector<int> active;
+    for (int i : g.members) {
+        if (finished[i]) continue;
+        // finish() may ask for a restart (true residual above tol); a restart
+        // that is converged at once is finished on the next pass
+        for (int pass = 0; pass < 16 && !finished[i]; pass++) {
+            if (!(sv[i].done || sv[i].inf.iters >= sv[i].P.maxiter)) break;
+            if (sv[i].finish(xdev[i], g.st)) {
+                finished[i] = true;
+                break;
+            }
+            sv[i].start_cg(g.st);
+        }
+        if (!finished[i] && !sv[i].done) active.push_back(i);
+    }
+    if (active.empty()) {
+        // finish() gives up after 8 restarts, so every member is finished here
+        for (int i : g.members)
+            if (!finished[i]) throw eofa_error(EOFA_EDEVICE, "batched solve: a system neither finished nor active");
+        return false;
+    }
+    if (active != g.captured) build_graph(g, sv, active);
+    for (size_t a = 0; a < active.size(); a++) {
+        const Solve& s = sv[active[a]];
+        const double thr = s.mixed ? std::max(s.delta * s.rmax, s.target) : s.target;
+        g.ctl_host[CTL_THR + a] = thr * thr;
+        g.ctl_host[CTL_RMAX + a] = s.mixed ? s.rmax * s.rmax : 1e300;
+        g.ctl_host[CTL_LEFT + a] = (double)(s.P.maxiter - s.inf.iters);
+    }
+    g.ctl_host[CTL_ITERS] = 0.0;
+    EOFA_CUDA(cudaMemcpyAsync(g.ctl, g.ctl_host, CTL_DOUBLES * sizeof(double), cudaMemcpyHostToDevice, g.st));
+    EOFA_CUDA(cudaGraphLaunch(g.exec, g.st));
+    EOFA_CUDA(cudaMemcpyAsync(g.ctl_host + CTL_RR, g.ctl + CTL_RR, (CTL_DOUBLES - CTL_RR) * sizeof(double),
+                              cudaMemcpyDeviceToHost, g.st));
+    EOFA_CUDA(cudaEventRecord(g.done, g.st));
+    g.running = true;
+    return true;
+}
+
+// The device loop of g has ended: account its iterations and run the host
+// checks (reliable updates, convergence) of every captured system.
+void collect_group(Group& g, std::vector<Solve>& sv) {
+    g.running = false;
+    const int n = (int)std::lround(g.ctl_host[CTL_ITERS]);
+    for (size_t a = 0; a < g.captured.size(); a++) {
+        Solve& s = sv[g.captured[a]];
+        s.it += n;
+        s.inf.iters += n;
+        s.check_value(g.ctl_host[CTL_RR + a], g.st);
+    }
+}
+
+}  // namespace
 
 extern "C" int eofa_solve_batched(eofa_ctx* const* ctxs, int n, const eofa_solve_params* params,
                                   const double* const* b, double* const* x, eofa_solve_info* info) {
@@ -25,114 +250,87 @@ extern "C" int eofa_solve_batched(eofa_ctx* const* ctxs, int n, const eofa_solve
         if (!ctxs[i] || !b[i] || !x[i]) return EOFA_EINVAL;
     auto t0 = std::chrono::steady_clock::now();
     eofa_ctx* errctx = ctxs[0];
-    std::vector<cudaStream_t> streams(n, nullptr);
-    cudaStream_t origin = nullptr;
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
-    std::vector<cudaEvent_t> evs;
-    std::vector<bool> prof_saved(n, false);
-    double* rr_host = nullptr;
+    std::vector<std::unique_ptr<Group>> groups;
     int rc = EOFA_OK;
     try {
         std::vector<Solve> sv(n);
         std::vector<double*> bdev(n), xdev(n);
-        EOFA_CUDA(cudaStreamCreateWithFlags(&origin, cudaStreamNonBlocking));
-        EOFA_CUDA(cudaMallocHost((void**)&rr_host, n * sizeof(double)));
+        std::vector<bool> finished(n, false);
+        // groups: same context and inner precision, at most MR_MAX systems each
+        std::map<std::pair<eofa_ctx*, int>, Group*> open;
         for (int i = 0; i < n; i++) {
             errctx = ctxs[i];
-            EOFA_CUDA(cudaStreamCreateWithFlags(&streams[i], cudaStreamNonBlocking));
-            size_t bytes = (size_t)ctxs[i]->V * ctxs[i]->Ls * 12 * 16;
-            std::string tg = "_b" + std::to_string(i);
-            bdev[i] = (double*)ctx_buffer(ctxs[i], "bt_b" + tg, bytes);
-            xdev[i] = (double*)ctx_buffer(ctxs[i], "bt_x" + tg, bytes);
-            double* red = (double*)ctx_buffer(ctxs[i], "bt_red" + tg, red_scratch_bytes());
-            EOFA_CUDA(cudaMemsetAsync(red, 0, red_scratch_bytes(), streams[i]));
-            EOFA_CUDA(cudaMemcpyAsync(bdev[i], b[i], bytes, cudaMemcpyHostToDevice, streams[i]));
-            if (params[i].use_x0) EOFA_CUDA(cudaMemcpyAsync(xdev[i], x[i], bytes, cudaMemcpyHostToDevice, streams[i]));
-            sv[i].setup(ctxs[i], params[i], bdev[i], xdev[i], tg, red, BATCH_CHUNK, streams[i]);
-            if (!sv[i].trivial) sv[i].start_cg(streams[i]);
+            const int prec = params[i].precision == EOFA_PREC_F64
+                                 ? P64
+                                 : (params[i].precision == EOFA_PREC_MIXED_F16 ? P16 : P32);
+            auto key = std::make_pair(ctxs[i], prec);
+            Group* g = open.count(key) ? open[key] : nullptr;
+            if (!g || (int)g->members.size() >= MR_MAX) {
+                groups.emplace_back(new Group());
+                g = groups.back().get();
+                g->ctx = ctxs[i];
+                g->prec = prec;
+                EOFA_CUDA(cudaStreamCreateWithFlags(&g->st, cudaStreamNonBlocking));
+                EOFA_CUDA(cudaEventCreateWithFlags(&g->done, cudaEventDisableTiming));
+                const std::string gt = "_g" + std::to_string(groups.size() - 1);
+                g->ops = (Op5*)ctx_buffer(g->ctx, "bt_ops" + gt, 2 * MR_MAX * sizeof(Op5));
+                g->ctl = (double*)ctx_buffer(g->ctx, "bt_ctl" + gt, CTL_DOUBLES * sizeof(double));
+                EOFA_CUDA(cudaMallocHost((void**)&g->ctl_host, CTL_DOUBLES * sizeof(double)));
+                open[key] = g;
+            }
+            g->members.push_back(i);
         }
-        // fork/join events, 2 per system
-        evs.resize(2 * n + 1);
-        for (auto& e : evs) EOFA_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-        std::vector<int> active, captured;
-        std::vector<bool> finished(n, false);
-        for (;;) {
-            active.clear();
-            for (int i = 0; i < n; i++) {
-                if (finished[i]) continue;
-                if (sv[i].done || sv[i].inf.iters >= sv[i].P.maxiter) {
-                    errctx = ctxs[i];
-                    if (sv[i].finish(xdev[i], streams[i])) {
-                        finished[i] = true;
-                        continue;
-                    }
-                    if (!sv[i].start_cg(streams[i])) continue;  // converged on restart: finish next round
-                }
-                active.push_back(i);
-            }
-            if (active.empty()) {
-                bool all = true;
-                for (int i = 0; i < n; i++) all = all && finished[i];
-                if (all) break;
-                continue;
-            }
-            if (active != captured) {
-                if (exec) EOFA_CUDA(cudaGraphExecDestroy(exec));
-                if (graph) EOFA_CUDA(cudaGraphDestroy(graph));
-                exec = nullptr;
-                graph = nullptr;
-                for (int i : active) EOFA_CUDA(cudaStreamSynchronize(streams[i]));
-                for (int i : active)
-                    if (ctxs[i]->prof) { prof_saved[i] = ctxs[i]->prof->on; ctxs[i]->prof->on = false; }
-                EOFA_CUDA(cudaStreamBeginCapture(origin, cudaStreamCaptureModeThreadLocal));
-                EOFA_CUDA(cudaEventRecord(evs[2 * n], origin));
-                for (int i : active) {
-                    EOFA_CUDA(cudaStreamWaitEvent(streams[i], evs[2 * n], 0));
-                    sv[i].enqueue(BATCH_CHUNK, streams[i]);
-                    EOFA_CUDA(cudaEventRecord(evs[2 * i], streams[i]));
-                    EOFA_CUDA(cudaStreamWaitEvent(origin, evs[2 * i], 0));
-                }
-                EOFA_CUDA(cudaStreamEndCapture(origin, &graph));
-                for (int i : active)
-                    if (ctxs[i]->prof) ctxs[i]->prof->on = prof_saved[i];
-                EOFA_CUDA(cudaGraphInstantiate(&exec, graph, 0));
-                captured = active;
-                // the capture advanced the counters by one chunk; the first launch runs that chunk
-            } else {
-                for (int i : active) {
-                    sv[i].it += BATCH_CHUNK;
-                    sv[i].inf.iters += BATCH_CHUNK;
-                }
-            }
-            // the graph runs on origin: order it after the host-side work queued on
-            // each system's stream (restarts, reliable updates)
-            for (int i : active) {
-                EOFA_CUDA(cudaEventRecord(evs[2 * i + 1], streams[i]));
-                EOFA_CUDA(cudaStreamWaitEvent(origin, evs[2 * i + 1], 0));
-            }
-            EOFA_CUDA(cudaGraphLaunch(exec, origin));
-            EOFA_CUDA(cudaStreamSynchronize(origin));
-            // each system's iteration counter stays a multiple of the chunk, so the
-            // parities and residual-ring slots baked into the graph stay valid;
-            // all residuals come back in one round trip
-            for (size_t a = 0; a < active.size(); a++)
-                EOFA_CUDA(cudaMemcpyAsync(rr_host + a, sv[active[a]].last_rr(), sizeof(double),
-                                          cudaMemcpyDeviceToHost, origin));
-            EOFA_CUDA(cudaStreamSynchronize(origin));
-            for (size_t a = 0; a < active.size(); a++) {
-                int i = active[a];
+        for (auto& gp : groups) {
+            Group& g = *gp;
+            for (int i : g.members) {
                 errctx = ctxs[i];
-                sv[i].check_value(rr_host[a], streams[i]);
+                size_t bytes = (size_t)ctxs[i]->V * ctxs[i]->Ls * 12 * 16;
+                std::string tg = "_b" + std::to_string(i);
+                bdev[i] = (double*)ctx_buffer(ctxs[i], "bt_b" + tg, bytes);
+                xdev[i] = (double*)ctx_buffer(ctxs[i], "bt_x" + tg, bytes);
+                double* red = (double*)ctx_buffer(ctxs[i], "bt_red" + tg, red_scratch_bytes());
+                EOFA_CUDA(cudaMemsetAsync(red, 0, red_scratch_bytes(), g.st));
+                EOFA_CUDA(cudaMemcpyAsync(bdev[i], b[i], bytes, cudaMemcpyHostToDevice, g.st));
+                if (params[i].use_x0) EOFA_CUDA(cudaMemcpyAsync(xdev[i], x[i], bytes, cudaMemcpyHostToDevice, g.st));
+                sv[i].setup(ctxs[i], params[i], bdev[i], xdev[i], tg, red, MR_BODY, g.st);
+                if (!sv[i].trivial) sv[i].start_cg(g.st);
             }
         }
+        for (auto& gp : groups) {
+            errctx = gp->ctx;
+            gp->finished = !service_group(*gp, sv, finished, xdev);
+        }
+        for (;;) {
+            bool any = false, progressed = false;
+            for (auto& gp : groups) {
+                Group& g = *gp;
+                if (g.finished) continue;
+                any = true;
+                if (!g.running) continue;
+                cudaError_t q = cudaEventQuery(g.done);
+                if (q == cudaErrorNotReady) continue;
+                EOFA_CUDA(q);
+                errctx = g.ctx;
+                progressed = true;
+                collect_group(g, sv);
+                g.finished = !service_group(g, sv, finished, xdev);
+            }
+            if (!any) break;
+            if (!progressed) std::this_thread::sleep_for(std::chrono::microseconds(20));
+        }
+        for (auto& gp : groups) {
+            for (int i : gp->members) {
+                errctx = ctxs[i];
+                size_t bytes = (size_t)ctxs[i]->V * ctxs[i]->Ls * 12 * 16;
+                EOFA_CUDA(cudaMemcpyAsync(x[i], xdev[i], bytes, cudaMemcpyDeviceToHost, gp->st));
+            }
+            EOFA_CUDA(cudaStreamSynchronize(gp->st));
+        }
+        const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
         for (int i = 0; i < n; i++) {
-            size_t bytes = (size_t)ctxs[i]->V * ctxs[i]->Ls * 12 * 16;
-            EOFA_CUDA(cudaMemcpyAsync(x[i], xdev[i], bytes, cudaMemcpyDeviceToHost, streams[i]));
-            EOFA_CUDA(cudaStreamSynchronize(streams[i]));
             eofa_solve_info inf = sv[i].inf;
             inf.true_resid = sv[i].true_rel;
-            inf.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+            inf.seconds = secs;
             inf.status = !std::isfinite(sv[i].true_rel) ? EOFA_ENUMERIC
                                                          : (sv[i].true_rel > sv[i].P.tol ? EOFA_ENOTCONV : EOFA_OK);
             if (info) info[i] = inf;
@@ -142,24 +340,16 @@ extern "C" int eofa_solve_batched(eofa_ctx* const* ctxs, int n, const eofa_solve
             }
         }
     } catch (const eofa_error& e) {
-        cudaStreamCaptureStatus cs;
-        if (origin && cudaStreamIsCapturing(origin, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) {
-            cudaGraph_t g = nullptr;
-            cudaStreamEndCapture(origin, &g);
-            if (g) cudaGraphDestroy(g);
-        }
         cudaGetLastError();
         rc = fail(errctx, e.code, e.msg);
     }
-    if (exec) cudaGraphExecDestroy(exec);
-    if (graph) cudaGraphDestroy(graph);
-    for (auto& e : evs) cudaEventDestroy(e);
-    for (auto& s : streams)
-        if (s) {
-            cudaStreamSynchronize(s);
-            cudaStreamDestroy(s);
-        }
-    if (origin) cudaStreamDestroy(origin);
-    if (rr_host) cudaFreeHost(rr_host);
+    for (auto& gp : groups) {
+        Group& g = *gp;
+        if (g.st) cudaStreamSynchronize(g.st);
+        destroy_graph(g);
+        if (g.done) cudaEventDestroy(g.done);
+        if (g.st) cudaStreamDestroy(g.st);
+        if (g.ctl_host) cudaFreeHost(g.ctl_host);
+    }
     return rc;
 }

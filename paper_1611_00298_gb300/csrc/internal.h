@@ -184,3 +184,5 @@ void blas_cg_update(const eofa_ctx* ctx, int prec, int prec_x, double alpha, con
                     void* r, int slot, cudaStream_t st);
 void blas_flat_dot(const eofa_ctx* ctx, long long ncplx, const double* a, const double* b, int slot, cudaStream_t st);
 size_t red_scratch_bytes();
+// resolve the no-allocation entry point's static scratch on device dev (noalloc.cu)
+void noalloc_prepare(int dev);

@@ -12,7 +12,7 @@
 
 #include <mutex>
 
-#define NOALLOC_SCRATCH_BYTES (16ull << 20)  // 16 MiB, held by every GPU that loads the library
+#define NOALLOC_SCRATCH_BYTES (16ull << 20)  // 16 MiB per device, taken when its first context is created
 #define NOALLOC_MAX_DEVICES 64
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
@@ -42,6 +42,13 @@ void* scratch_on(int dev) {
 inline size_t round256(size_t n) { return (n + 255) & ~size_t(255); }
 
 }  // namespace
+
+// Called by eofa_create with the context's device current.  CUDA loads this
+// file's module (and with it the 16 MiB array) lazily, on the first use of
+// one of its symbols; resolving the address here makes that load, and its
+// allocation, happen while the context is created (a call that allocates
+// anyway), so that eofa_dwf_apply_noalloc itself never loads a module.
+void noalloc_prepare(int dev) { (void)scratch_on(dev); }
 
 extern "C" int eofa_dwf_apply_noalloc(eofa_ctx* ctx, int Ls, double alpha, double M5, double mf, int dagger,
                                       const double* in_dev, double* out_dev, void* stream) {

@@ -33,7 +33,7 @@ EXPORTS = [
     "eofa_dwf_apply_noalloc", "eofa_schur_hop_dev", "eofa_pseudofermion_solutions_dev",
     "eofa_set_reliable_delta", "eofa_leapfrog_dev", "eofa_rational_inv_sqrt", "eofa_heatbath_dev",
     "eofa_gauge_action_dev", "eofa_gauge_force_dev", "eofa_hmc_trajectory_dev", "eofa_force_parts_dev",
-    "eofa_check_device",
+    "eofa_check_device", "eofa_hmc_dev",
 ]
 INT_LEAPFROG, INT_FG_PQPQP, INT_FG_QPQPQ = 0, 1, 2
 
@@ -69,6 +69,15 @@ class MDInfo(ctypes.Structure):
                 ("kinetic1", ctypes.c_double), ("S_gauge0", ctypes.c_double), ("S_gauge1", ctypes.c_double),
                 ("S_eofa0", ctypes.c_double), ("S_eofa1", ctypes.c_double), ("fermion_forces", ctypes.c_int),
                 ("gauge_forces", ctypes.c_int), ("solver_iters", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class HMCTrajInfo(ctypes.Structure):
+    _fields_ = [("H0", ctypes.c_double), ("dH", ctypes.c_double), ("exp_minus_dH", ctypes.c_double),
+                ("accepted", ctypes.c_int), ("plaquette", ctypes.c_double), ("S_eofa_start", ctypes.c_double),
+                ("eta_norm2", ctypes.c_double), ("solver_iters", ctypes.c_int), ("seconds", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -134,6 +143,7 @@ def load_library(path: str = LIB_PATH):
         "eofa_rational_inv_sqrt": (I, [I, D, D, ctypes.POINTER(D), P, P, ctypes.POINTER(D)]),
         "eofa_heatbath_dev": (I, [P, I, D, D, D, D, I, D, I, D, P, P, P, P, I, ctypes.POINTER(SolveInfo), P]),
         "eofa_leapfrog_dev": (I, [P, I, D, D, D, D, I, D, I, D, P, P, P, ctypes.POINTER(D), ctypes.POINTER(D), P]),
+        "eofa_hmc_dev": (I, [P, ctypes.POINTER(MDParams), I, D, I, P, P, P, P, P, P, ctypes.POINTER(HMCTrajInfo), P]),
         "eofa_profile_start": (I, [P]),
         "eofa_profile_stop": (I, [P, ctypes.POINTER(Profile)]),
     }
@@ -271,13 +281,18 @@ class Lattice:
         return SolveParams(self.Ls, alpha, M5, system, mf, m1, m2, shift, precision, tol, maxiter, delta,
                            int(use_x0))
 
-    def solve(self, b, x0=None, **kw):
+    def solve(self, b, x0=None, check=True, **kw):
+        """Solve one system; with check=False a failure status is returned in info.status
+        instead of raised."""
         b = np.ascontiguousarray(b, dtype=np.complex128)
         p = self.solve_params(use_x0=x0 is not None, **kw)
         x = np.zeros_like(b) if x0 is None else np.ascontiguousarray(x0, dtype=np.complex128).copy()
         info = SolveInfo()
         rc = self.lib.eofa_solve(self.ctx, ctypes.byref(p), _ptr(b), _ptr(x), ctypes.byref(info))
-        self._check(rc, "solve")
+        if check:
+            self._check(rc, "solve")
+        else:
+            info.status = rc
         return x, info
 
     def action(self, phi, alpha, M5, m1, m2, precision=PREC_F64, tol=1e-10):
@@ -330,11 +345,14 @@ class Lattice:
         self._check(self.lib.eofa_dwf_apply_noalloc(self.ctx, self.Ls, alpha, M5, mf, int(dagger), _ptr(psi),
                                                     _ptr(out), _stream()), "dwf_apply_noalloc")
 
-    def solve_dev(self, b, x, use_x0=False, **kw):
+    def solve_dev(self, b, x, use_x0=False, check=True, **kw):
         p = self.solve_params(use_x0=use_x0, **kw)
         info = SolveInfo()
         rc = self.lib.eofa_solve_dev(self.ctx, ctypes.byref(p), _ptr(b), _ptr(x), ctypes.byref(info), _stream())
-        self._check(rc, "solve_dev")
+        if check:
+            self._check(rc, "solve_dev")
+        else:
+            info.status = rc
         return info
 
     def action_dev(self, phi, alpha, M5, m1, m2, precision=PREC_F64, tol=1e-10):
@@ -442,13 +460,39 @@ class Lattice:
         self._check(rc, "hmc_trajectory_dev")
         return info.as_dict()
 
+    def hmc_dev(self, Ps, etas, us, U=None, *, alpha=2.0, M5=1.8, m1=0.04, m2=1.0, precision=PREC_F64, tol=1e-10,
+                beta=0.0, integrator=INT_FG_QPQPQ, nsteps=4, tau=1.0, n_inner=0, split_lr=False, n_middle=0,
+                rational=None):
+        """HMC chain of len(us) trajectories: heatbath refresh of phi from etas[k] (rational =
+        (alpha0, alphas, betas) of f ~ x^-1/2; None: pure gauge, no pseudofermion), momenta Ps[k],
+        Metropolis with us[k].  Ps, etas: device tensors with the trajectories stacked on the first
+        axis.  The context's links end at the chain's last state; returns the list of records."""
+        prm = MDParams(self.Ls, alpha, M5, m1, m2, precision, tol, beta, integrator, nsteps, tau, n_inner,
+                       int(split_lr), n_middle)
+        u = np.ascontiguousarray(us, dtype=np.float64)
+        n = len(u)
+        if rational is None:
+            a0, al, be, npoles = 0.0, np.zeros(1), np.zeros(1), 0
+        else:
+            a0 = float(rational[0])
+            al = np.ascontiguousarray(rational[1], dtype=np.float64)
+            be = np.ascontiguousarray(rational[2], dtype=np.float64)
+            npoles = len(al)
+        info = (HMCTrajInfo * max(1, n))()
+        rc = self.lib.eofa_hmc_dev(self.ctx, ctypes.byref(prm), n, a0, npoles, al.ctypes.data, be.ctypes.data,
+                                   _ptr(Ps), _ptr(etas) if etas is not None else None, u.ctypes.data,
+                                   _ptr(U) if U is not None else None, info, _stream())
+        self._check(rc, "hmc_dev")
+        return [info[k].as_dict() for k in range(n)]
+
     def link_update_dev(self, eps, P, U=None):
         self._check(self.lib.eofa_link_update_dev(self.ctx, eps, _ptr(P), _ptr(U) if U is not None else None,
                                                   _stream()), "link_update_dev")
 
 
-def solve_batched(lattices, params, bs, xs):
-    """Solve len(lattices) systems; params: list of SolveParams; bs, xs: numpy arrays."""
+def solve_batched(lattices, params, bs, xs, check=True):
+    """Solve len(lattices) systems; params: list of SolveParams; bs, xs: numpy arrays.
+    With check=False a failure status is left in the info records instead of raised."""
     lib = load_library()
     n = len(lattices)
     ctxs = (ctypes.c_void_p * n)(*[lat.ctx.value for lat in lattices])
@@ -457,6 +501,6 @@ def solve_batched(lattices, params, bs, xs):
     xp = (ctypes.c_void_p * n)(*[_ptr(x) for x in xs])
     info = (SolveInfo * n)()
     rc = lib.eofa_solve_batched(ctxs, n, prm, bp, xp, info)
-    if rc not in (OK,):
+    if check and rc != OK:
         raise EOFAError(rc, "solve_batched")
     return info

@@ -199,3 +199,84 @@ def test_mixed_precision_trajectory_matches_fp64(eofa):
     assert np.abs(P32 - P64).max() < 1e-7
     assert abs(dH32 - dH64) < 1e-6 * max(1.0, abs(dH64))
     lat.close()
+
+
+# ---------------------------------------------------------------- the HMC chain (Metropolis)
+
+def _rational_fit(n, lmin, lmax):
+    """Some rational f(x) = alpha0 + sum_l alpha_l / (x + beta_l) close to x^-1/2
+    on [lmin, lmax] (least squares at fixed poles); the chain comparison only
+    needs both sides to use the same f."""
+    betas = np.geomspace(lmin, lmax, n)
+    x = np.geomspace(lmin / 2, lmax * 2, 600)
+    A = np.column_stack([np.ones_like(x)] + [1.0 / (x + b) for b in betas]) * np.sqrt(x)[:, None]
+    c = np.linalg.lstsq(A, np.ones_like(x), rcond=None)[0]
+    return c[0], c[1:], betas
+
+
+def test_hmc_chain_matches_oracle_chain(eofa):
+    """Four trajectories on 2^4 x Ls=4 from the same random numbers on both
+    sides (momenta, heatbath noise, Metropolis uniforms): heatbath refresh of
+    phi, nested QPQPQ trajectory with the EOFA and Wilson gauge forces,
+    accept/reject.  The decisions, dH, the start action and the final links
+    agree with the oracle chain; the chain has both outcomes."""
+    import torch
+    dims, Ls, ntraj = (2, 2, 2, 2), 4, 4
+    U0 = inputs.gauge_field(dims, 0.4, 31)
+    Ps = [inputs.momenta(dims, 32, stream=10 + k) for k in range(ntraj)]
+    etas = [inputs.fermion4d(dims, 33, stream=20 + k) for k in range(ntraj)]
+    us = inputs.uniform(inputs.stream_key(34, 1), ntraj)
+    rational = _rational_fit(10, 1e-2, 10.0)
+    fermion = dict(Ls=Ls, alpha=ALPHA, M5=M5, m1=M1, m2=M2, bc_t=-1.0, tol=1e-13)
+    Uo, recs = gauge.hmc_chain(U0, Ps, us, BETA, 1.0, 1, "qpqpq", n_inner=2, fermion=fermion, etas=etas,
+                               rational=rational)
+    assert {r[1] for r in recs} == {True, False}
+    lat = eofa.Lattice(dims, Ls)
+    lat.gauge_load(U0)
+    Pd = _dev(np.stack(Ps))
+    etad = _dev(np.stack(etas))
+    Ud = torch.empty(U0.shape, dtype=torch.complex128, device="cuda")
+    info = lat.hmc_dev(Pd, etad, us, Ud, alpha=ALPHA, M5=M5, m1=M1, m2=M2, tol=1e-13, beta=BETA,
+                       integrator=eofa.INT_FG_QPQPQ, nsteps=1, tau=1.0, n_inner=2, rational=rational)
+    for k, (dH, acc, S0) in enumerate(recs):
+        assert bool(info[k]["accepted"]) == acc, (k, info[k], recs[k])
+        assert info[k]["dH"] == pytest.approx(dH, abs=1e-8 * max(1.0, abs(dH)))
+        assert info[k]["S_eofa_start"] == pytest.approx(S0, rel=1e-10)
+        assert info[k]["eta_norm2"] == pytest.approx(np.vdot(etas[k], etas[k]).real, rel=1e-12)
+        assert info[k]["exp_minus_dH"] == pytest.approx(np.exp(-dH), rel=1e-7)
+    assert np.abs(Ud.cpu().numpy() - Uo).max() < 1e-10
+    # the context's links are the chain's state
+    Ud2 = torch.empty_like(Ud)
+    lat.hmc_dev(Pd[:1], etad[:1], [0.0], Ud2, alpha=ALPHA, M5=M5, m1=M1, m2=M2, tol=1e-13, beta=BETA,
+                integrator=eofa.INT_FG_QPQPQ, nsteps=1, tau=1.0, n_inner=2, rational=rational)
+    U5, _ = gauge.hmc_chain(Uo, Ps[:1], [0.0], BETA, 1.0, 1, "qpqpq", n_inner=2, fermion=fermion, etas=etas[:1],
+                            rational=rational)
+    assert np.abs(Ud2.cpu().numpy() - U5).max() < 1e-10
+    lat.close()
+
+
+def test_hmc_chain_pure_gauge_and_bad_arguments(eofa):
+    """npoles = 0 runs a pure-gauge chain (same records as the oracle's); the
+    uniforms must lie in [0, 1)."""
+    import torch
+    dims = (2, 2, 2, 2)
+    U0 = inputs.gauge_field(dims, 0.3, 1)
+    n = 12
+    Ps = [inputs.momenta(dims, 200, stream=10 + k) for k in range(n)]
+    us = inputs.uniform(inputs.stream_key(200, 9), n)
+    Uo, recs = gauge.hmc_chain(U0, Ps, us, BETA, 1.0, 2, "leapfrog")
+    lat = eofa.Lattice(dims, 4)
+    lat.gauge_load(U0)
+    Ud = torch.empty(U0.shape, dtype=torch.complex128, device="cuda")
+    info = lat.hmc_dev(_dev(np.stack(Ps)), None, us, Ud, beta=BETA, integrator=eofa.INT_LEAPFROG, nsteps=2,
+                       tau=1.0)
+    assert [bool(i["accepted"]) for i in info] == [r[1] for r in recs]
+    assert 0 < sum(r[1] for r in recs) < n
+    for i, r in zip(info, recs):
+        assert i["dH"] == pytest.approx(r[0], abs=1e-9)
+    assert np.abs(Ud.cpu().numpy() - Uo).max() < 1e-11
+    with pytest.raises(eofa.EOFAError):
+        lat.hmc_dev(_dev(np.stack(Ps[:1])), None, [1.0], None, beta=BETA)
+    with pytest.raises(eofa.EOFAError):
+        lat.hmc_dev(_dev(np.stack(Ps[:1])), None, [0.5], None, beta=0.0)
+    lat.close()

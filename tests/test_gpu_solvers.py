@@ -131,3 +131,55 @@ def test_force_matches_oracle(eofa, alpha):
     lat.force_from_chi_dev(k, torch.from_numpy(chiL).cuda(), torch.from_numpy(chiR).cuda(), Fd)
     torch.cuda.synchronize()
     assert _rel(Fd.cpu().numpy(), Fo2) < 1e-12
+
+
+# ---------------------------------------------------------------- failure statuses (host-side inputs only)
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_solve_maxiter_reports_not_converged(eofa, prec):
+    """maxiter = 1 cannot reach 1e-10: EOFA_ENOTCONV, with info filled and x the current iterate."""
+    dims, Ls = (4, 4, 4, 4), 8
+    lat, U = _setup(eofa, dims, Ls)
+    b = inputs.fermion5d(dims, Ls, 7)
+    x, info = lat.solve(b, check=False, system=eofa.SYS_DWF, alpha=ALPHA, M5=M5, mf=M1, precision=prec, tol=1e-10,
+                        maxiter=1)
+    assert info.status == eofa.ENOTCONV
+    assert info.iters == 1
+    assert 1e-10 < info.true_resid < 1.0
+    res = np.linalg.norm(b - dwf.dwf(U, x, ALPHA, M5, M1, -1)) / np.linalg.norm(b)
+    assert abs(res - info.true_resid) < 1e-6 * res
+    msg = lat.lib.eofa_last_error(lat.ctx).decode()
+    assert "did not reach tol" in msg
+    lat.close()
+
+
+def test_solve_nan_source_reports_numeric(eofa):
+    dims, Ls = (4, 4, 4, 4), 8
+    lat, _ = _setup(eofa, dims, Ls)
+    b = inputs.fermion5d(dims, Ls, 8)
+    b.reshape(-1)[17] = np.nan
+    _, info = lat.solve(b, check=False, system=eofa.SYS_EOFA_L, alpha=ALPHA, M5=M5, m1=M1, m2=M2, precision=1,
+                        tol=1e-10)
+    assert info.status == eofa.ENUMERIC
+    with pytest.raises(eofa.EOFAError) as ei:
+        lat.solve(b, system=eofa.SYS_DWF, alpha=ALPHA, M5=M5, mf=M1, precision=0, tol=1e-10)
+    assert ei.value.code == eofa.ENUMERIC
+    # the context stays usable
+    b2 = inputs.fermion5d(dims, Ls, 9)
+    _, info2 = lat.solve(b2, system=eofa.SYS_DWF, alpha=ALPHA, M5=M5, mf=M1, precision=1, tol=1e-10)
+    assert info2.status == eofa.OK and info2.true_resid <= 1e-10
+    lat.close()
+
+
+@pytest.mark.parametrize("system", [0, 1, 2])
+def test_solve_zero_source_returns_zero(eofa, system):
+    dims, Ls = (4, 4, 2, 4), 6
+    lat, _ = _setup(eofa, dims, Ls)
+    b = np.zeros(lat.shape5, dtype=np.complex128)
+    x0 = inputs.fermion5d(dims, Ls, 10)  # overwritten: the solution of a zero source is zero
+    x, info = lat.solve(b, x0=x0, system=system, alpha=ALPHA, M5=M5, mf=M1, m1=M1, m2=M2,
+                        shift=-1.0 if system == 2 else 0.0, precision=1, tol=1e-10)
+    assert info.status == eofa.OK
+    assert info.iters == 0
+    assert np.count_nonzero(x) == 0
+    lat.close()

@@ -119,3 +119,59 @@ def test_nested_integrator_order_and_reversibility():
     U2, P2, dH2 = gauge.trajectory(U1, -P1, f, 0.5, 3, "qpqpq", 2)
     assert np.abs(U2 - U).max() < 1e-11
     assert np.abs(P2 + P).max() < 1e-11
+
+
+# ---------------------------------------------------------------- HMC chain (Sec. 3, Sec. 5)
+
+def test_metropolis_accept_rule():
+    """Accept with probability min(1, exp(-dH)): u < exp(-dH)."""
+    assert gauge.metropolis(-0.5, 0.999999)          # dH <= 0 always accepted
+    assert gauge.metropolis(0.0, 0.999999)
+    assert gauge.metropolis(0.7, 0.49)               # exp(-0.7) = 0.4966
+    assert not gauge.metropolis(0.7, 0.50)
+    assert not gauge.metropolis(3.0, 0.05)           # exp(-3) = 0.0498
+    assert gauge.metropolis(3.0, 0.049)
+    assert not gauge.metropolis(float("nan"), 0.0)
+    assert not gauge.metropolis(float("inf"), 0.0)
+
+
+def _pure_gauge_chain(n, warm, nsteps=8, scheme="leapfrog", seed=200):
+    dims = (2, 2, 2, 2)
+    U = inputs.gauge_field(dims, 0.3, 1)
+    Ps = [inputs.momenta(dims, seed, stream=10 + k) for k in range(n + warm)]
+    us = inputs.uniform(inputs.stream_key(seed, 9), n + warm)
+    U1, recs = gauge.hmc_chain(U, Ps, us, BETA, 1.0, nsteps, scheme)
+    return U, Ps, us, U1, recs
+
+
+def test_hmc_chain_keeps_the_links_of_a_rejected_trajectory():
+    """Step by step: an accepted trajectory moves the links to the trajectory's
+    end point, a rejected one leaves them bit for bit; the decision is the
+    Metropolis rule on that trajectory's dH."""
+    U, Ps, us, _, _ = _pure_gauge_chain(0, 12, nsteps=2)  # coarse steps: some rejections
+    f = gauge.Forces(BETA)
+    rejected = 0
+    for k in range(12):
+        Un, recs = gauge.hmc_chain(U, [Ps[k]], [us[k]], BETA, 1.0, 2, "leapfrog")
+        U1, _, dH = gauge.trajectory(U, Ps[k], f, 1.0, 2, "leapfrog")
+        assert recs[0][0] == dH
+        assert recs[0][1] == (us[k] < np.exp(-dH))
+        if recs[0][1]:
+            assert np.array_equal(Un, U1)
+        else:
+            assert np.array_equal(Un, U)
+            rejected += 1
+        U = Un
+    assert 0 < rejected < 12
+
+
+def test_hmc_chain_creutz_equality_pure_gauge():
+    """In equilibrium <exp(-dH)> = 1 (area preservation and reversibility of
+    the integrator) and <dH> > 0; 300 trajectories after 60 of warm-up on 2^4
+    at beta = 5.7 (8 leapfrog steps, acceptance about 0.9)."""
+    _, _, _, _, recs = _pure_gauge_chain(300, 60)
+    dH = np.array([r[0] for r in recs])[60:]
+    e = np.exp(-dH)
+    err = e.std() / np.sqrt(len(e))
+    assert abs(e.mean() - 1.0) < 4 * err, (e.mean(), err)
+    assert dH.mean() > 0, dH.mean()

@@ -140,3 +140,16 @@ def test_force_part_pin_catches_a_swapped_sign(monkeypatch):
     monkeypatch.setattr(oeofa, "force_from_chi", flipped)
     with pytest.raises(AssertionError):
         t.test_force_parts_match_partial_action_differences(U)
+
+
+def test_creutz_pin_catches_a_flipped_metropolis_sign(monkeypatch):
+    """Accepting with exp(+dH) drives the chain away from exp(-S): <dH> turns negative."""
+    monkeypatch.setattr(gauge, "metropolis", lambda dH, u: bool(np.isfinite(dH) and u < np.exp(dH)))
+    dims = (2, 2, 2, 2)
+    U = inputs.gauge_field(dims, 0.3, 1)
+    n, warm = 300, 60
+    Ps = [inputs.momenta(dims, 200, stream=10 + k) for k in range(n + warm)]
+    us = inputs.uniform(inputs.stream_key(200, 9), n + warm)
+    _, recs = gauge.hmc_chain(U, Ps, us, BETA, 1.0, 8, "leapfrog")
+    dH = np.array([r[0] for r in recs])[warm:]
+    assert not dH.mean() > 0
