@@ -108,52 +108,112 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def cpu_baseline(U, wl, budget_s=20.0):
-    """The FP64 oracle's Wilson dslash on a bounded sample of the workload (host cores)."""
+def cpu_baseline(U, wl, cg_iters=2):
+    """The oracle (plain FP64 C restatement of D_w, D_DWF and CGNR, oracle/c) on the host cores.
+
+    Timed: one D_w on the whole lattice with every core, the same on a 2-slice
+    sample with one core, and cg_iters CGNR iterations on D_DWF (Eq. (3)) with
+    every core, reported per iteration.  GB/s counts the same algorithmic
+    bytes per 5D site as the GPU's FP64 hop."""
     import numpy as np
 
-    from oracle import dwf
+    from oracle import c_oracle
     from paper_1611_00298_gb300 import inputs
 
     X, Y, Z, T = wl["dims"]
-    ns = 2  # s-slices in the sample
-    psi = inputs.fermion5d(wl["dims"], ns, wl["seed"], stream=9)
+    Ls = wl["Ls"]
+    V = X * Y * Z * T
+    bps = hop_bytes_per_site(0, Ls)
+    cores = c_oracle.threads()
+    psi = inputs.fermion5d(wl["dims"], Ls, wl["seed"], stream=9)
     t0 = time.perf_counter()
-    reps = 0
-    while True:
-        dwf.wilson(U, psi, wl["M5"], wl["bc"])
-        reps += 1
-        if time.perf_counter() - t0 > budget_s / 2 or reps >= 3:
-            break
-    dt = (time.perf_counter() - t0) / reps
-    sites = ns * X * Y * Z * T
-    gbs = sites * hop_bytes_per_site(0, wl["Ls"]) / dt / 1e9
+    c_oracle.wilson(U, psi, wl["M5"], wl["bc"])
+    t_all = time.perf_counter() - t0
+    c_oracle.set_threads(1)
+    try:
+        sample = np.ascontiguousarray(psi[:2])
+        t0 = time.perf_counter()
+        c_oracle.wilson(U, sample, wl["M5"], wl["bc"])
+        t_one = time.perf_counter() - t0
+    finally:
+        c_oracle.set_threads(cores)
+    _, it, _, t_cg = c_oracle.cgnr_dwf(U, psi, wl["alpha"], wl["M5"], wl["m1"], wl["bc"], tol=1e-30,
+                                       maxiter=cg_iters, timing=True)
     del np
-    return {"value": round(gbs, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
-            "sample": f"numpy FP64 D_w (both parities) on {ns} of {wl['Ls']} s-slices of {X}x{Y}x{Z}x{T}, "
-                      f"{reps} reps, {dt:.2f} s each; bytes counted as for the FP64 hop at Ls={wl['Ls']}"}
+    return {"value": round(V * Ls * bps / t_all / 1e9, 4), "unit": "GB/s", "cores": cores, "kind": "oracle",
+            "single_core_GBs": round(V * 2 * bps / t_one / 1e9, 4),
+            "cg_iteration_seconds": round(t_cg / max(1, it), 3), "cg_iterations_timed": it,
+            "sample": f"C oracle (oracle/c/dwf_oracle.c, gcc -O2, OpenMP): D_w on the whole {X}x{Y}x{Z}x{T} x "
+                      f"Ls={Ls} lattice with {cores} threads ({t_all:.2f} s); the same on 2 of {Ls} s-slices "
+                      f"with 1 thread ({t_one:.2f} s); {it} CGNR iterations on D_DWF (m_f={wl['m1']}) with "
+                      f"{cores} threads, {t_cg:.2f} s in total; bytes counted as for the FP64 hop"}
 
 
 def run_reference(args, wl, rank):
+    """The oracle on the host cores, per step one D_w on the whole lattice (all cores)."""
     if rank != 0:
         return 0
+    from oracle import c_oracle
     from paper_1611_00298_gb300 import inputs
     U = inputs.gauge_field(wl["dims"], wl["eps"], wl["seed"])
-    vals = []
-    cb = None
+    psi = inputs.fermion5d(wl["dims"], wl["Ls"], wl["seed"], stream=9)
+    X, Y, Z, T = wl["dims"]
+    nbytes = X * Y * Z * T * wl["Ls"] * hop_bytes_per_site(0, wl["Ls"])
+    times = []
     for i in range(args.warmup + args.steps):
-        cb = cpu_baseline(U, wl, budget_s=10.0)
+        t0 = time.perf_counter()
+        c_oracle.wilson(U, psi, wl["M5"], wl["bc"])
         if i >= args.warmup:
-            vals.append(cb["value"])
-    v = statistics.mean(vals)
-    cb["value"] = round(v, 4)
+            times.append(time.perf_counter() - t0)
+    v = nbytes * len(times) / sum(times) / 1e9
+    cores = c_oracle.threads()
+    cb = {"value": round(v, 4), "unit": "GB/s", "cores": cores, "kind": "oracle",
+          "sample": f"C oracle D_w on the whole {X}x{Y}x{Z}x{T} x Ls={wl['Ls']} lattice per step, {cores} threads"}
     line = {"impl": "reference", "metric": METRIC, "value": round(v, 4), "unit": "GB/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_config(wl, "oracle FP64 Wilson dslash sample"),
-            "cpu_baseline": cb, "e2e": {"value": round(v, 4), "unit": "GB/s", "h2d_bytes_per_step": 0,
-                                        "d2h_bytes_per_step": 0}}
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1000 * sum(times) / len(times), 2),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(wl), "cpu_baseline": cb,
+            "e2e": {"value": round(v, 4), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+    return 0
+
+
+def fp64_peak_bench(args, wl):
+    """FP64 FMA rate of the GPU (probe kernel, CUDA events) and the FP64 hop's flop rate against it."""
+    import torch
+
+    from paper_1611_00298_gb300 import build, eofa, inputs
+    if not os.path.exists(eofa.LIB_PATH):
+        build.build()
+    peak = eofa.probe_fp64_fma()
+    U = inputs.gauge_field(wl["dims"], wl["eps"], wl["seed"])
+    lat = eofa.Lattice(wl["dims"], wl["Ls"], bc_t=wl["bc"])
+    lat.gauge_load(U)
+    del U
+    canon = torch.randn(lat.V * wl["Ls"] * 24, dtype=torch.float64, device="cuda")
+    nb = lat.field_bytes(0)
+    e = torch.empty(nb, dtype=torch.uint8, device="cuda")
+    o = torch.empty_like(e)
+    out = torch.empty_like(e)
+    lat.pack_dev(0, canon, e, o)
+    del canon
+    for _ in range(3):
+        lat.hop_dev(0, 0, 0, o, out)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for _ in range(args.hop_reps):
+        lat.hop_dev(0, 0, 0, o, out)
+    ev1.record()
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / args.hop_reps
+    n5h = lat.V // 2 * wl["Ls"]
+    tf = 1320.0 * n5h / (ms / 1000) / 1e12
+    print(json.dumps({"fp64_fma_tflops": round(peak, 3), "fp64_hop_ms": round(ms, 3), "fp64_hop_tflops": round(tf, 3),
+                      "fp64_hop_frac_of_measured_fma": round(tf / peak, 3),
+                      "lattice": "x".join(map(str, wl["dims"])), "Ls": wl["Ls"],
+                      "flops_per_site": 1320}), flush=True)
+    lat.close()
     return 0
 
 
@@ -283,7 +343,9 @@ def hmc_chain_bench(args):
     if not os.path.exists(eofa.LIB_PATH):
         build.build()
     dims, Ls, beta = (8, 8, 8, 8), 8, 5.7
-    n_therm, n_traj = 60, args.chain_traj
+    # the random start relaxes over a few hundred pure-gauge trajectories (cheap); the
+    # plaquette must have stopped drifting before <exp(-dH)> means anything
+    n_therm, n_traj = 600, args.chain_traj
     U = inputs.gauge_field(dims, 0.5, 41)
     lat = eofa.Lattice(dims, Ls, bc_t=-1)
     lat.gauge_load(U)
@@ -294,11 +356,19 @@ def hmc_chain_bench(args):
     t_therm = time.perf_counter() - t0
     del Pth
     a0, al, be, err = eofa.rational_inv_sqrt(12, 1e-3, 20.0)
-    Ps = torch.from_numpy(np.stack([inputs.momenta(dims, 43, stream=10 + k) for k in range(n_traj)])).cuda()
-    etas = torch.from_numpy(np.stack([inputs.fermion4d(dims, 44, stream=10 + k) for k in range(n_traj)])).cuda()
-    us = inputs.uniform(inputs.stream_key(45, 1), n_traj)
     kw = dict(alpha=2.0, M5=1.8, m1=0.04, m2=1.0, precision=eofa.PREC_MIXED_F32, tol=1e-10, beta=beta,
               integrator=eofa.INT_FG_QPQPQ, nsteps=4, tau=1.0, n_inner=2)
+
+    def draws(n, seed):
+        Ps = torch.from_numpy(np.stack([inputs.momenta(dims, seed, stream=10 + k) for k in range(n)])).cuda()
+        etas = torch.from_numpy(np.stack([inputs.fermion4d(dims, seed + 1, stream=10 + k) for k in range(n)])).cuda()
+        return Ps, etas, inputs.uniform(inputs.stream_key(seed + 2, 1), n)
+    # the fermion changes the equilibrium: thermalise with it before measuring
+    n_therm_f = 24
+    t0 = time.perf_counter()
+    thf = lat.hmc_dev(*draws(n_therm_f, 50), rational=(a0, al, be), **kw)
+    t_therm_f = time.perf_counter() - t0
+    Ps, etas, us = draws(n_traj, 43)
     t0 = time.perf_counter()
     info = lat.hmc_dev(Ps, etas, us, rational=(a0, al, be), **kw)
     t_chain = time.perf_counter() - t0
@@ -308,8 +378,14 @@ def hmc_chain_bench(args):
            "alpha": 2.0, "integrator": "nested force-gradient QPQPQ (4 EOFA steps, 2 gauge steps each), tau = 1",
            "heatbath": f"12-pole Zolotarev x^-1/2 on [1e-3, 20], max rel err {err:.1e}",
            "thermalisation": {"trajectories": n_therm, "acceptance": float(np.mean([i["accepted"] for i in th])),
-                              "plaquette_end": th[-1]["plaquette"], "seconds": round(t_therm, 2)},
+                              "plaquette_end": th[-1]["plaquette"],
+                              "plaquette_last_100_mean": float(np.mean([i["plaquette"] for i in th[-100:]])),
+                              "seconds": round(t_therm, 2)},
+           "thermalisation_with_eofa": {"trajectories": n_therm_f,
+                                        "acceptance": float(np.mean([i["accepted"] for i in thf])),
+                                        "dH": [round(i["dH"], 4) for i in thf], "seconds": round(t_therm_f, 2)},
            "trajectories": n_traj, "acceptance": float(np.mean([i["accepted"] for i in info])),
+           "dH": [round(i["dH"], 4) for i in info],
            "exp_minus_dH_mean": float(e.mean()), "exp_minus_dH_err": float(e.std(ddof=1) / np.sqrt(len(e))),
            "dH_mean": float(dH.mean()), "dH_rms": float(np.sqrt(np.mean(dH ** 2))),
            "plaquette_mean": float(np.mean([i["plaquette"] for i in info])),
@@ -364,13 +440,13 @@ def batched(args):
         t, info = run_batched(eofa.PREC_MIXED_F32)
         tb.append(t)
     ts32, _ = run_sequential(eofa.PREC_MIXED_F32)
-    ts64, its64 = run_sequential(eofa.PREC_F64)
+    ts64, its64 = run_sequential(eofa.PREC_F64) if not args.no_fp64 else (float("nan"), [])
     worst = max(i.true_resid for i in info)
     out = {"metric": "batched EOFA/DWF solves per second (24 solves, 3 lattices, true residual 1e-10)",
            "value": round(len(bs) / statistics.mean(tb), 3), "unit": "solves/s", "n_gpus": 1,
            "batched_mixed_f32_seconds": round(statistics.mean(tb), 4),
            "sequential_mixed_f32_seconds": round(ts32, 4), "sequential_fp64_seconds": round(ts64, 4),
-           "fp64_sequential_over_batched": round(ts64 / statistics.mean(tb), 2),
+           "fp64_sequential_over_batched": round(ts64 / statistics.mean(tb), 2) if not args.no_fp64 else None,
            "worst_true_resid": worst, "iters": [i.iters for i in info], "fp64_iters": its64,
            "config": {"workload": "8^4x8, 12^4x12, 16^3x32x16 (eps 0.5, seeds 5, 6, 7); mass pairs (0.04,0.2), "
                                   "(0.2,0.6), (0.6,1.0) x {L, R} + D_DWF at m_f 0.04, 0.2 per lattice"}}
@@ -378,11 +454,13 @@ def batched(args):
     return 0
 
 
-def workload_config(wl, what):
+def workload_config(wl):
     X, Y, Z, T = wl["dims"]
     return {"workload": f"EOFA force evaluation, {X}^3x{T} Ls={wl['Ls']} Moebius alpha={wl['alpha']} "
                         f"M5={wl['M5']} m1={wl['m1']} m2={wl['m2']}, synthetic links eps={wl['eps']} seed {wl['seed']}",
-            "lattice": f"{X}x{Y}x{Z}x{T}", "Ls": wl["Ls"], "what": what, "global_batch": 1,
+            "lattice": f"{X}x{Y}x{Z}x{T}", "Ls": wl["Ls"], "global_batch": 1,
+            "what": "dslash GB/s: algorithmic bytes of the even-odd Wilson hops (one input and one output spinor "
+                    "per 5D site, links once per 4D site) per second",
             "l2": "inputs larger than L2 (each FP32 half-checkerboard field is 1.02 GB)",
             "parallelism": "replicas (one independent lattice per GPU)"}
 
@@ -414,6 +492,7 @@ def main():
     ap.add_argument("--small", action="store_true", help="8^4 x 8 lattice (quick check)")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 solve comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--cpu-cg-iters", type=int, default=2, help="CGNR iterations of the CPU oracle baseline")
     ap.add_argument("--hop-only", action="store_true",
                     help="only launch the even-odd hop kernel (for ncu captures); see --dims, --hop-reps")
     ap.add_argument("--dims", default=None, help="X,Y,Z,T override for --hop-only")
@@ -426,6 +505,8 @@ def main():
     ap.add_argument("--hmc", action="store_true",
                     help="one nested force-gradient QPQPQ trajectory at 16^3x32, Ls=12 (EOFA + Wilson gauge), "
                          "one level and split L/R")
+    ap.add_argument("--fp64-peak", action="store_true",
+                    help="measured FP64 FMA rate (the ALU roofline of the FP64 hop) and the FP64 hop against it")
     ap.add_argument("--hmc-chain", action="store_true",
                     help="HMC chain at 8^4, Ls=8: pure-gauge thermalisation, then EOFA trajectories with heatbath "
                          "refresh and Metropolis; acceptance and <exp(-dH)>")
@@ -447,6 +528,8 @@ def main():
         return hmc_bench(args)
     if args.hmc_chain:
         return hmc_chain_bench(args)
+    if args.fp64_peak:
+        return fp64_peak_bench(args, wl)
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -583,13 +666,14 @@ def main():
             "warmup": args.warmup, "ms_per_step": round(1000 * t_max / args.steps, 2), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
             "data": "synthetic (seeded SU(3) links and Gaussian pseudofermion; no ensemble)",
-            "config": workload_config(wl, f"mixed {args.precision.upper()} inner CG, FP64 reliable updates"),
+            "config": workload_config(wl),
+            "solver": f"mixed {args.precision.upper()} inner CG, FP64 reliable updates",
             "roofline": roofline, "e2e": e2e, "solve": solve, "clocks": clk, "gpu_launches": int(launches),
             "hop_launches_by_precision": {"fp64": hop_launches[0], "fp32": hop_launches[1], "fp16": hop_launches[2]},
             "action": actions[-1],
         }
         if not args.no_cpu:
-            result["cpu_baseline"] = cpu_baseline(U, wl)
+            result["cpu_baseline"] = cpu_baseline(U, wl, args.cpu_cg_iters)
         print(json.dumps(result), flush=True)
     if dist is not None:
         dist.barrier()

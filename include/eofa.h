@@ -381,6 +381,10 @@ typedef struct {
     double bytes[6];
 } eofa_profile;
 long long eofa_kernel_launches(void);
+/* Measured FP64 fused multiply-add rate of the current device in TFLOP/s
+ * (2 flops per FMA; 8 independent chains per thread, best of 3 timed
+ * launches): the ALU roofline of the FP64 hop.  Allocates 8 bytes. */
+int eofa_probe_fp64_fma(double* tflops);
 int eofa_profile_start(eofa_ctx* ctx);
 int eofa_profile_stop(eofa_ctx* ctx, eofa_profile* out);
 

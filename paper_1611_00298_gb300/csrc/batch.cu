@@ -5,9 +5,9 @@
 //
 // Systems on the same lattice and with the same inner precision form a
 // group (at most MR_MAX systems).  A group iterates its systems in lock
-// step with the multi-system kernels of mrhs.cuh: one launch per CG step
-// for all of them, each link row and neighbour index fetched once for the
-// whole group.  The CG loop of a group runs on the device: a CUDA graph
+// step with the multi-system kernels of mrhs.cuh: the five launches of the
+// CG iteration of solver.cu, each for all of them, each link row and
+// neighbour index fetched once for the whole group.  The CG loop of a group runs on the device: a CUDA graph
 // holds one WHILE conditional node whose body is K CG iterations of every
 // active system followed by a one-block decision kernel; the kernel reads
 // each system's |r|^2 and keeps the loop going until some system has
@@ -21,6 +21,8 @@
 #include "solver.h"
 
 #include <chrono>
+#include <cstdio>
+#include <cstdlib>
 #include <cmath>
 #include <map>
 #include <memory>
@@ -63,18 +65,12 @@ __global__ void mr_decide_kernel(MRPtrs a, int nr, double* ctl, cudaGraphConditi
     if (threadIdx.x == 0) cudaGraphSetConditional(h, stop ? 0u : 1u);
 }
 
-void mr_dslash(const eofa_ctx* ctx, int prec, int par, int dag, const MRPtrs& a, const Op5* ops, int nr, bool hasop,
-               double a_out, double b_in, int slot, cudaStream_t st) {
-    if (prec == P64) mr_dslash_p64(ctx, par, dag, a, ops, nr, hasop, a_out, b_in, slot, st);
-    else if (prec == P32) mr_dslash_p32(ctx, par, dag, a, ops, nr, hasop, a_out, b_in, slot, st);
-    else mr_dslash_p16(ctx, par, dag, a, ops, nr, hasop, a_out, b_in, slot, st);
-}
-
-void mr_local5(const eofa_ctx* ctx, int prec, const MRPtrs& a, const Op5* ops, int nr, int it, int slot,
+void mr_dslash(const eofa_ctx* ctx, int prec, int par, int dag, int mode, const MRPtrs& a, const Op5* ops,
+               const Op5* ops2, int nr, bool hasop, double a_out, double b_in, int slot, int it, int slot2,
                cudaStream_t st) {
-    if (prec == P64) mr_local5_p64(ctx, a, ops, nr, it, slot, st);
-    else if (prec == P32) mr_local5_p32(ctx, a, ops, nr, it, slot, st);
-    else mr_local5_p16(ctx, a, ops, nr, it, slot, st);
+    if (prec == P64) mr_dslash_p64(ctx, par, dag, mode, a, ops, ops2, nr, hasop, a_out, b_in, slot, it, slot2, st);
+    else if (prec == P32) mr_dslash_p32(ctx, par, dag, mode, a, ops, ops2, nr, hasop, a_out, b_in, slot, it, slot2, st);
+    else mr_dslash_p16(ctx, par, dag, mode, a, ops, ops2, nr, hasop, a_out, b_in, slot, it, slot2, st);
 }
 
 void mr_xp(const eofa_ctx* ctx, int prec, const MRPtrs& a, int nr, int it, cudaStream_t st) {
@@ -97,32 +93,34 @@ struct Group {
     double* ctl_host = nullptr;  // pinned mirror
     bool running = false;
     bool finished = false;
+    // diagnostics (EOFA_BATCH_LOG=1): host visits, graph builds, host seconds
+    int visits = 0, builds = 0;
+    double host_s = 0.0, build_s = 0.0;
 };
 
-// One lock-step CG iteration (it) of the captured systems: the six fused
+// One lock-step CG iteration (it) of the captured systems: the five fused
 // launches of Solve::enqueue, each for all systems at once.
 void enqueue_group_iteration(Group& g, std::vector<Solve>& sv, int it, cudaStream_t st) {
     const int n = (int)g.captured.size();
-    MRPtrs k1 = {}, k2 = {}, k3 = {}, k4 = {}, k5 = {}, k6 = {};
+    MRPtrs k1 = {}, k2 = {}, k4 = {}, k5 = {}, k6 = {};
     for (int a = 0; a < n; a++) {
         Solve& s = sv[g.captured[a]];
         k1.in[a] = s.p;  k1.out[a] = s.te; k1.red[a] = s.red;
-        k2.in[a] = s.te; k2.out[a] = s.q;  k2.y[a] = s.p;   k2.red[a] = s.red;
-        k3.out2[a] = s.r; k3.y[a] = s.q;   k3.out[a] = s.to; k3.red[a] = s.red;
+        k2.in[a] = s.te; k2.out[a] = s.q;  k2.y[a] = s.p;   k2.out2[a] = s.to; k2.red[a] = s.red;
         k4.in[a] = s.to; k4.out[a] = s.te; k4.red[a] = s.red;
-        k5.in[a] = s.te; k5.out[a] = s.s;  k5.y[a] = s.r;   k5.red[a] = s.red;
+        k5.in[a] = s.te; k5.out[a] = s.s;  k5.y[a] = s.q;   k5.out2[a] = s.r; k5.red[a] = s.red;
         k6.out2[a] = s.x; k6.out[a] = s.p; k6.in[a] = s.s;  k6.red[a] = s.red;
     }
     const Op5* Gi = g.ops;
     const Op5* GiT = g.ops + MR_MAX;
-    // q = A p: te = G'^-1 D_eo p; q = p - G'^-1 D_oe te, |q|^2 -> delta
-    mr_dslash(g.ctx, g.prec, 0, 0, k1, Gi, n, true, 1.0, 0.0, -1, st);
-    mr_dslash(g.ctx, g.prec, 1, 0, k2, Gi, n, true, -1.0, 1.0, SC_DELTA, st);
-    // r -= alpha q, |r|^2 -> ring; to = G'^-T r
-    mr_local5(g.ctx, g.prec, k3, GiT, n, it, SC_RRH + (it % MR_BODY), st);
-    // s = A^+ r: te = G'^-T D^+_eo to; s = r - D^+_oe te, |s|^2 -> gamma (next parity)
-    mr_dslash(g.ctx, g.prec, 0, 1, k4, GiT, n, true, 1.0, 0.0, -1, st);
-    mr_dslash(g.ctx, g.prec, 1, 1, k5, GiT, n, false, -1.0, 1.0, SC_GAMMA + ((it + 1) & 1), st);
+    // q = A p: te = G'^-1 D_eo p; q = p - G'^-1 D_oe te, |q|^2 -> delta, to = G'^-T q
+    mr_dslash(g.ctx, g.prec, 0, 0, 0, k1, Gi, GiT, n, true, 1.0, 0.0, -1, it, -1, st);
+    mr_dslash(g.ctx, g.prec, 1, 0, 1, k2, Gi, GiT, n, true, -1.0, 1.0, SC_DELTA, it, -1, st);
+    // s -= alpha A^+ q: te = G'^-T D^+_eo to; s -= alpha (q - D^+_oe te), |s|^2 -> gamma (next
+    // parity); r -= alpha q, |r|^2 -> ring
+    mr_dslash(g.ctx, g.prec, 0, 1, 0, k4, GiT, GiT, n, true, 1.0, 0.0, -1, it, -1, st);
+    mr_dslash(g.ctx, g.prec, 1, 1, 2, k5, GiT, GiT, n, false, -1.0, 1.0, SC_GAMMA + ((it + 1) & 1), it,
+              SC_RRH + (it % MR_BODY), st);
     // x += alpha p; p = s + beta p
     mr_xp(g.ctx, g.prec, k6, n, it, st);
 }
@@ -138,6 +136,8 @@ void destroy_graph(Group& g) {
 // Graph of the group's device loop for the active set: WHILE(cond) { MR_BODY
 // iterations; decide }.
 void build_graph(Group& g, std::vector<Solve>& sv, const std::vector<int>& active) {
+    auto t0 = std::chrono::steady_clock::now();
+    g.builds++;
     destroy_graph(g);
     g.captured = active;
     const int n = (int)active.size();
@@ -182,6 +182,7 @@ void build_graph(Group& g, std::vector<Solve>& sv, const std::vector<int>& activ
     }
     if (g.ctx->prof) g.ctx->prof->on = prof_on;
     EOFA_CUDA(cudaGraphInstantiate(&g.exec, g.graph, 0));
+    g.build_s += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
 }
 
 // Retire, restart or keep the group's systems after a host check; launch the
@@ -312,8 +313,11 @@ extern "C" int eofa_solve_batched(eofa_ctx* const* ctxs, int n, const eofa_solve
                 EOFA_CUDA(q);
                 errctx = g.ctx;
                 progressed = true;
+                auto th = std::chrono::steady_clock::now();
+                g.visits++;
                 collect_group(g, sv);
                 g.finished = !service_group(g, sv, finished, xdev);
+                g.host_s += std::chrono::duration<double>(std::chrono::steady_clock::now() - th).count();
             }
             if (!any) break;
             if (!progressed) std::this_thread::sleep_for(std::chrono::microseconds(20));
@@ -327,6 +331,11 @@ extern "C" int eofa_solve_batched(eofa_ctx* const* ctxs, int n, const eofa_solve
             EOFA_CUDA(cudaStreamSynchronize(gp->st));
         }
         const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        if (getenv("EOFA_BATCH_LOG"))
+            for (size_t k = 0; k < groups.size(); k++)
+                fprintf(stderr, "batch group %zu: V=%d Ls=%d prec=%d systems=%zu visits=%d builds=%d host %.3f s (builds %.3f s) of %.3f s\n",
+                        k, groups[k]->ctx->V, groups[k]->ctx->Ls, groups[k]->prec, groups[k]->members.size(),
+                        groups[k]->visits, groups[k]->builds, groups[k]->host_s, groups[k]->build_s, secs);
         for (int i = 0; i < n; i++) {
             eofa_solve_info inf = sv[i].inf;
             inf.true_resid = sv[i].true_rel;

@@ -49,3 +49,32 @@ void fused_xp_update(const eofa_ctx* ctx, int prec, int precx, const double* sc,
     else if (prec == P32) xp_update_p32(ctx, sc, it, x, p, s, st);
     else xp_update_p16(ctx, sc, it, x, p, s, st);
 }
+
+void fused_dslash_to(const eofa_ctx* ctx, int prec, int out_parity, int dagger, const void* in, void* out,
+                     const Op5& op, const void* y, double a_out, double b_in, double* red, int slot, const Op5& op2,
+                     void* out2, cudaStream_t st) {
+    const Op5 opf = op_finalize(op, ctx->Ls);
+    const Op5 op2f = op_finalize(op2, ctx->Ls);
+    const double n5h = (double)ctx->Vh * ctx->Ls;
+    // in, out, out2 (+ y): one spinor each per output site, links once per 4D site
+    const double bytes = n5h * spinor_bytes(prec) * (y ? 4.0 : 3.0) + 8.0 * ctx->Vh * (prec == P64 ? 144.0 : 72.0);
+    prof_begin(ctx, prec, st, bytes);
+    if (prec == P64) dslash_to_p64(ctx, out_parity, dagger, in, out, opf, y, a_out, b_in, red, slot, op2f, out2, st);
+    else if (prec == P32) dslash_to_p32(ctx, out_parity, dagger, in, out, opf, y, a_out, b_in, red, slot, op2f, out2, st);
+    else dslash_to_p16(ctx, out_parity, dagger, in, out, opf, y, a_out, b_in, red, slot, op2f, out2, st);
+    prof_end(ctx, st);
+}
+
+void fused_dslash_z(const eofa_ctx* ctx, int prec, int out_parity, int dagger, const void* in, void* z, const Op5& op,
+                    const void* y, double a_out, double b_in, double* red, int slot, int it, void* r, int rslot,
+                    cudaStream_t st) {
+    const Op5 opf = op_finalize(op, ctx->Ls);
+    const double n5h = (double)ctx->Vh * ctx->Ls;
+    // in, y, z and r read, z and r written
+    const double bytes = n5h * spinor_bytes(prec) * 6.0 + 8.0 * ctx->Vh * (prec == P64 ? 144.0 : 72.0);
+    prof_begin(ctx, prec, st, bytes);
+    if (prec == P64) dslash_z_p64(ctx, out_parity, dagger, in, z, opf, y, a_out, b_in, red, slot, it, r, rslot, st);
+    else if (prec == P32) dslash_z_p32(ctx, out_parity, dagger, in, z, opf, y, a_out, b_in, red, slot, it, r, rslot, st);
+    else dslash_z_p16(ctx, out_parity, dagger, in, z, opf, y, a_out, b_in, red, slot, it, r, rslot, st);
+    prof_end(ctx, st);
+}

@@ -46,6 +46,33 @@
 namespace dsl {
 namespace {
 
+// ---------------------------------------------------------------- packed FP32 pairs
+// (re, im) of one complex number in a 64-bit register; the f32x2 instructions
+// do two FP32 multiply-adds each (used by the 5D-local recurrences; the same
+// form in the link products of the hop measured slower).
+#ifndef EOFA_PACKED_F32
+#define EOFA_PACKED_F32 1
+#endif
+typedef unsigned long long f2p;
+__device__ __forceinline__ f2p splat2(float a) {
+    f2p r;
+    asm("mov.b64 %0, {%1, %1};" : "=l"(r) : "f"(a));
+    return r;
+}
+__device__ __forceinline__ f2p fma2(f2p a, f2p b, f2p c) {
+    f2p r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+__device__ __forceinline__ f2p mul2(f2p a, f2p b) {
+    f2p r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2p ld2(const cpx<float>* p) { return *reinterpret_cast<const f2p*>(p); }
+__device__ __forceinline__ void st2(cpx<float>* p, f2p v) { *reinterpret_cast<f2p*>(p) = v; }
+
+
 // ---------------------------------------------------------------- hop pieces
 
 template <int MU, typename R>
@@ -340,28 +367,6 @@ __device__ __forceinline__ void col_stream(const Half<R>& H, cpx<R>* col) {
 // FP32 form of col_stream on packed pairs: every step multiplies a complex
 // number by real coefficients, so (re, im) travel as one 64-bit register and
 // each complex multiply-add is one f32x2 instruction.
-#ifndef EOFA_PACKED_F32
-#define EOFA_PACKED_F32 1
-#endif
-typedef unsigned long long f2p;
-__device__ __forceinline__ f2p splat2(float a) {
-    f2p r;
-    asm("mov.b64 %0, {%1, %1};" : "=l"(r) : "f"(a));
-    return r;
-}
-__device__ __forceinline__ f2p fma2(f2p a, f2p b, f2p c) {
-    f2p r;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
-    return r;
-}
-__device__ __forceinline__ f2p mul2(f2p a, f2p b) {
-    f2p r;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-    return r;
-}
-__device__ __forceinline__ f2p ld2(const cpx<float>* p) { return *reinterpret_cast<const f2p*>(p); }
-__device__ __forceinline__ void st2(cpx<float>* p, f2p v) { *reinterpret_cast<f2p*>(p) = v; }
-
 template <int LS, bool R1>
 __device__ __forceinline__ void col_stream_f2(const Half<float>& H, cpx<float>* col) {
     const f2p MR = splat2(H.mr), NM = splat2(-H.mass), INVN = splat2(H.invN), NQ = splat2(-H.q1),
@@ -432,6 +437,143 @@ __device__ __forceinline__ void column_op(const Op5& op, int c, cpx<R>* col, int
     }
 }
 
+// 1: at Ls >= 16 (even) two neighbouring lanes share each FP32 column of
+// the 5D-local block, each running the recurrences over half of s
+#ifndef EOFA_COL_SPLIT
+#define EOFA_COL_SPLIT 0
+#endif
+
+__device__ __forceinline__ f2p shfl_pair(f2p v) { return __shfl_xor_sync(0xffffffffu, v, 1); }
+__device__ __forceinline__ f2p add_pair(f2p v) {
+    f2p r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(v), "l"(shfl_pair(v)));
+    return r;
+}
+
+// Streaming form of the block (as col_stream_f2) on one FP32 column by a
+// lane pair: lane half = 0 takes t in [0, Lh), half = 1 takes [Lh, Ls) in the
+// recurrence's own order t (t = s for the down-shift, Ls - 1 - s for the
+// up-shift).  The corner sum is split and joined with mr^Lh; the inverse
+// recurrence u_t = invp x_t + mr u_{t-1} runs in both halves at once, the
+// upper half from zero, then adds mr^(t - Lh + 1) u_{Lh-1}; the last values
+// of each half cross by one shuffle.  Every lane of the warp calls this (act
+// = false: a lane pair without a column computes on column 0 and writes
+// nothing), so the shuffles see full warps.
+template <int LS, bool R1>
+__device__ __forceinline__ void col_split_f2(const Half<float>& H, cpx<float>* col, int half, bool act) {
+    constexpr int LH = LS / 2;
+    const int dir = H.dir1;
+    auto at = [&](int t) { return dir == 0 ? t : LS - 1 - t; };
+    const f2p MR = splat2(H.mr), INVP = splat2(H.invp);
+    const float p2 = H.fwd ? H.p2 : 1.f, q2 = H.fwd ? H.q2 : 0.f;
+    const f2p P2 = splat2(p2), Q2 = splat2(q2), Q2M = splat2(-q2 * H.mass);
+    const int t0 = half ? LH : 0;
+    // corner sum: sum_{t>=1} mr^(Ls-t) x_t = mr^Lh A0 + A1
+    f2p acc = 0ull;
+#pragma unroll
+    for (int k = 0; k < LH; k++) {
+        const int t = t0 + k;
+        if (t >= 1) acc = fma2(MR, acc, ld2(col + at(t)));
+    }
+    acc = mul2(MR, acc);
+    float mrh = 1.f;
+#pragma unroll
+    for (int k = 0; k < LH; k++) mrh *= H.mr;
+    const f2p other = shfl_pair(acc);
+    const f2p total = half ? fma2(splat2(mrh), other, acc) : fma2(splat2(mrh), acc, other);
+    // inverse recurrence; the lower half starts from u_0, the upper from zero
+    f2p u;
+    if (half == 0) {
+        u = mul2(splat2(H.invN), fma2(splat2(-H.mass), total, ld2(col + at(0))));
+        if (act) st2(col + at(0), u);
+    } else {
+        u = 0ull;
+    }
+#pragma unroll
+    for (int k = (half == 0 ? 1 : 0); k < LH; k++) {
+        const int t = t0 + k;
+        u = fma2(MR, u, mul2(INVP, ld2(col + at(t))));
+        if (act) st2(col + at(t), u);
+    }
+    // u_{Lh-1} to the upper half, which adds mr^(t - Lh + 1) u_{Lh-1}
+    const f2p ulow = shfl_pair(u);
+    f2p d = 0ull;
+    if (half == 1) {
+        f2p pw = MR;
+#pragma unroll
+        for (int k = 0; k < LH; k++) {
+            const int t = LH + k;
+            const f2p v = fma2(pw, ulow, ld2(col + at(t)));
+            if (act) st2(col + at(t), v);
+            if (R1) d = fma2(splat2(H.v[at(t)]), v, d);
+            pw = mul2(pw, MR);
+        }
+    } else if (R1) {
+#pragma unroll
+        for (int k = 0; k < LH; k++) d = fma2(splat2(H.v[at(k)]), ld2(col + at(k)), d);
+    }
+    // u_{Ls-1} from the upper half (its last value after the fix-up)
+    const f2p ulast_up = half == 1 ? ld2(col + at(LS - 1)) : 0ull;
+    const f2p ulast = shfl_pair(ulast_up);
+    const f2p uprev_low = shfl_pair(u);  // the lower half's u_{Lh-1} for the upper half's first output
+    // out_t = p2 u_t + q2 u_{t-1}, out_0 = p2 u_0 - q2 mass u_{Ls-1}; downwards so that u_{t-1} is still there
+#pragma unroll
+    for (int k = LH - 1; k >= 0; k--) {
+        const int t = t0 + k;
+        const f2p ut = ld2(col + at(t));
+        f2p o;
+        if (t == 0) o = fma2(P2, ut, mul2(Q2M, ulast));
+        else if (k == 0) o = fma2(P2, ut, mul2(Q2, uprev_low));
+        else o = fma2(P2, ut, mul2(Q2, ld2(col + at(t - 1))));
+        if (act) st2(col + at(t), o);
+    }
+    if (R1) {
+        // rank-one term: out += sigma w (v . u), v . u summed over both halves
+        d = mul2(splat2(H.sigma), add_pair(d));
+#pragma unroll
+        for (int k = 0; k < LH; k++) {
+            const int t = t0 + k;
+            if (act) st2(col + at(t), fma2(splat2(H.w[at(t)]), d, ld2(col + at(t))));
+        }
+    }
+}
+
+// Lane-pair form of the column loop of a tile: every lane takes part.
+template <int LS>
+__device__ __forceinline__ void columns_split_f2(const Op5& op, cpx<float>* sm, int ncols, int LsP, const float* wv) {
+    const int per = blockDim.x >> 1;
+    const int half = threadIdx.x & 1;
+    for (int base = 0; base < ncols; base += per) {
+        const int idx = base + (threadIdx.x >> 1);
+        const bool act = idx < ncols;
+        const int c = act ? idx % 12 : 0;
+        const Half<float> H = half_of<float>(op, c < 6 ? 0 : 1, wv, LS);
+        cpx<float>* col = sm + (act ? idx : 0) * LsP;
+        if (H.sigma == 0.f) col_split_f2<LS, false>(H, col, half, act);
+        else col_split_f2<LS, true>(H, col, half, act);
+    }
+}
+
+// whether the lane-pair column form applies to this block (every column
+// uses the streaming form of col_stream)
+__device__ __forceinline__ bool split_ok(const Op5& op) {
+    for (int h = 0; h < 2; h++)
+        if (!op.inv[h] || (op.fwd[h] && op.dir2[h] != op.dir1[h])) return false;
+    return true;
+}
+
+// the column phase of a tile: lane pairs where they apply, one lane per column otherwise
+template <typename R, int LS>
+__device__ __forceinline__ void columns(const Op5& op, cpx<R>* sm, int ncols, int LsP, int Ls, const R* wv) {
+    if constexpr (EOFA_COL_SPLIT && std::is_same<R, float>::value && LS >= 16 && LS % 2 == 0) {
+        if (split_ok(op)) {
+            columns_split_f2<LS>(op, sm, ncols, LsP, wv);
+            return;
+        }
+    }
+    for (int idx = threadIdx.x; idx < ncols; idx += blockDim.x) column_op<R, LS>(op, idx % 12, sm + idx * LsP, Ls, wv);
+}
+
 __device__ __forceinline__ bool op_is_identity(const Op5& op) {
     return !op.inv[0] && !op.inv[1] && !op.fwd[0] && !op.fwd[1] && op.sigma[0] == 0.0 && op.sigma[1] == 0.0;
 }
@@ -477,6 +619,60 @@ __device__ __noinline__ void grid_sum(double v, double* red, int slot) {
     }
 }
 
+// Two sums at once: v1 -> red[slot1] (partials at RED_PART), v2 -> red[slot2]
+// (partials at RED_PART2); one ticket, fixed-order final sums.
+__device__ __noinline__ void grid_sum2(double v1, double v2, double* red, int slot1, int slot2) {
+    __shared__ double ws[2][32];
+    __shared__ bool last;
+    v1 = warp_sum(v1);
+    v2 = warp_sum(v2);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = (blockDim.x + 31) >> 5;
+    if (l == 0) {
+        ws[0][w] = v1;
+        ws[1][w] = v2;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t1 = 0, t2 = 0;
+        for (int k = 0; k < nw; k++) {
+            t1 += ws[0][k];
+            t2 += ws[1][k];
+        }
+        red[RED_PART + blockIdx.x] = t1;
+        red[RED_PART2 + blockIdx.x] = t2;
+        __threadfence();
+        unsigned prev = atomicAdd((unsigned*)(red + RED_TICKET), 1u);
+        last = prev == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (last) {
+        __threadfence();
+        double t1 = 0, t2 = 0;
+        for (int k = threadIdx.x; k < (int)gridDim.x; k += blockDim.x) {
+            t1 += ((volatile double*)red)[RED_PART + k];
+            t2 += ((volatile double*)red)[RED_PART2 + k];
+        }
+        t1 = warp_sum(t1);
+        t2 = warp_sum(t2);
+        __syncthreads();
+        if (l == 0) {
+            ws[0][w] = t1;
+            ws[1][w] = t2;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double f1 = 0, f2 = 0;
+            for (int k = 0; k < nw; k++) {
+                f1 += ws[0][k];
+                f2 += ws[1][k];
+            }
+            red[slot1] = f1;
+            red[slot2] = f2;
+            *(unsigned*)(red + RED_TICKET) = 0u;
+        }
+    }
+}
+
 template <typename R>
 __device__ __forceinline__ double site_norm2(const cpx<R>* v) {
     R a = 0;
@@ -497,15 +693,31 @@ __device__ __forceinline__ double cg_beta(const double* sc, int it) {
 
 // ---------------------------------------------------------------- fused dslash
 
+// Extra epilogue of the CG launches with more than one output (MODE 1, 2).
+struct Epi {
+    Op5 op2;        // MODE 1: block of the second output
+    void* out2;     // MODE 1: out2 = B2 out;  MODE 2: r, updated in place (r -= alpha y)
+    int it, slot2;  // MODE 2: iteration of the CG scalars, slot of |r|^2
+};
+
 // HASOP = false: B is the identity (plain hop), compiled separately so that
 // the register budget of the hop is not set by the 5D-local recurrences.
+// MODE 0: out = value.  MODE 1: also out2 = B2 out (a second 5D-local pass
+// through shared memory).  MODE 2: out is updated in place,
+// out <- out - alpha(red, it) value, and so is out2 <- out2 - alpha y, with
+// |out|^2 -> red[slot] and |out2|^2 -> red[ep.slot2].
 // SPT slices per thread: thread (site, sh) handles s = sh + k Ls/SPT,
 // k < SPT, so neighbour indices and link rows are loaded once for SPT output
 // sites (Ls/SPT threads per site; SPT = 2 needs an even Ls).
-template <int P, int DAG, int LS, bool HASOP, int SPT>
-__global__ void __launch_bounds__(256, SPT == 2 ? 2 : (HASOP ? EOFA_DSLASH_MINB : EOFA_HOP_MINB)) dslash_kernel(
+// the two-pass epilogue of MODE 1 gets up to 128 registers (its 80-register
+// build spilled 224 bytes)
+#ifndef EOFA_MODE1_MINB
+#define EOFA_MODE1_MINB 2
+#endif
+template <int P, int DAG, int LS, bool HASOP, int SPT, int MODE = 0>
+__global__ void __launch_bounds__(256, SPT == 2 ? 2 : (MODE == 1 ? EOFA_MODE1_MINB : (HASOP ? EOFA_DSLASH_MINB : EOFA_HOP_MINB))) dslash_kernel(
     Geom g, int par, const void* __restrict__ in, void* out, const void* __restrict__ gauge, Op5 op, const void* y,
-    double a_out, double b_in, double* red, int slot, int NS) {
+    double a_out, double b_in, double* red, int slot, int NS, Epi ep) {
     typedef typename Field<P>::R R;
     extern __shared__ __align__(16) unsigned char smraw[];
     cpx<R>* sm = reinterpret_cast<cpx<R>*>(smraw);
@@ -513,10 +725,11 @@ __global__ void __launch_bounds__(256, SPT == 2 ? 2 : (HASOP ? EOFA_DSLASH_MINB 
     const int LsP = Ls + 1;
     const int Lt = Ls / SPT;  // threads per site
     __shared__ R wv_s[HASOP ? 4 * EOFA_MAX_LS : 1];
-    if (HASOP) {
-        stage_wv<R>(op, Ls, wv_s);
-        __syncthreads();
-    }
+    __shared__ R wv2_s[MODE == 1 ? 4 * EOFA_MAX_LS : 1];
+    if (HASOP) stage_wv<R>(op, Ls, wv_s);
+    if (MODE == 1) stage_wv<R>(ep.op2, Ls, wv2_s);
+    if (HASOP || MODE == 1) __syncthreads();
+    const R cz = MODE == 2 ? (R)(-cg_alpha(red, ep.it)) : R(0);
     const long long n5 = (long long)g.Vh * Ls;
     const int ls = threadIdx.x / Lt, sh = threadIdx.x - ls * Lt;
     int sv[SPT];
@@ -525,7 +738,7 @@ __global__ void __launch_bounds__(256, SPT == 2 ? 2 : (HASOP ? EOFA_DSLASH_MINB 
     const bool active_thread = ls < NS;
     const int ntiles = (g.Vh + NS - 1) / NS;
     const R scale = (R)(-0.5 * a_out);
-    double nacc = 0.0;
+    double nacc = 0.0, nacc2 = 0.0;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int j = tile * NS + ls;
         const bool site_ok = active_thread && j < g.Vh;
@@ -557,8 +770,7 @@ __global__ void __launch_bounds__(256, SPT == 2 ? 2 : (HASOP ? EOFA_DSLASH_MINB 
             }
             __syncthreads();
             const int nsites = min(NS, g.Vh - tile * NS);
-            for (int idx = threadIdx.x; idx < nsites * 12; idx += blockDim.x)
-                column_op<R, LS>(op, idx % 12, sm + idx * LsP, Ls, wv_s);
+            columns<R, LS>(op, sm, nsites * 12, LsP, Ls, wv_s);
             __syncthreads();
             if (site_ok) {
 #pragma unroll
@@ -579,15 +791,50 @@ __global__ void __launch_bounds__(256, SPT == 2 ? 2 : (HASOP ? EOFA_DSLASH_MINB 
                     const R bb = (R)b_in;
 #pragma unroll
                     for (int c = 0; c < 12; c++) acc[k][c] = acc[k][c] + bb * yv[c];
+                    if (MODE == 2) {
+                        // r <- r - alpha y
+                        cpx<R> rv[12];
+                        Field<P>::load_stream(ep.out2, j, sv[k], Ls, n5, rv);
+#pragma unroll
+                        for (int c = 0; c < 12; c++) rv[c] = rv[c] + cz * yv[c];
+                        Field<P>::store_stream(ep.out2, j, sv[k], Ls, n5, rv);
+                        nacc2 += site_norm2<R>(rv);
+                    }
+                }
+                if (MODE == 2) {
+                    cpx<R> zv[12];
+                    Field<P>::load_stream(out, j, sv[k], Ls, n5, zv);
+#pragma unroll
+                    for (int c = 0; c < 12; c++) acc[k][c] = zv[c] + cz * acc[k][c];
                 }
                 if (EOFA_STREAM_HINTS) Field<P>::store_stream(out, j, sv[k], Ls, n5, acc[k]);
                 else Field<P>::store(out, j, sv[k], Ls, n5, acc[k]);
                 if (red) nacc += site_norm2<R>(acc[k]);
             }
         }
+        if (MODE == 1) {
+            // out2 = B2 out: the block's outputs go through shared memory once more
+            __syncthreads();
+            if (site_ok) {
+#pragma unroll
+                for (int c = 0; c < 12; c++) sts(sm + (ls * 12 + c) * LsP + sv[0], acc[0][c]);
+            }
+            __syncthreads();
+            const int nsites = min(NS, g.Vh - tile * NS);
+            columns<R, LS>(ep.op2, sm, nsites * 12, LsP, Ls, wv2_s);
+            __syncthreads();
+            if (site_ok) {
+#pragma unroll
+                for (int c = 0; c < 12; c++) acc[0][c] = lds(sm + (ls * 12 + c) * LsP + sv[0]);
+                Field<P>::store_stream(ep.out2, j, sv[0], Ls, n5, acc[0]);
+            }
+        }
         if (HASOP) __syncthreads();
     }
-    if (red) grid_sum(nacc, red, slot);
+    if (red) {
+        if (MODE == 2) grid_sum2(nacc, nacc2, red, slot, ep.slot2);
+        else grid_sum(nacc, red, slot);
+    }
 }
 
 // x' = x + c z (c = -alpha from the device scalars when use_alpha, else c0);
@@ -738,7 +985,25 @@ void launch_with(K k, const eofa_ctx* ctx, const Geom& g, int NS, int spt, size_
     const int ntiles = (g.Vh + NS - 1) / NS;
     if (smem > 40 * 1024) EOFA_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     unsigned grid = grid_size(k, threads, smem, ntiles, ctx->sms);
-    k<<<grid, threads, smem, st>>>(g, par, in, out, gauge, op, y, a_out, b_in, red, slot, NS);
+    Epi ep;
+    ep.op2 = op;
+    ep.out2 = nullptr;
+    ep.it = 0;
+    ep.slot2 = 0;
+    k<<<grid, threads, smem, st>>>(g, par, in, out, gauge, op, y, a_out, b_in, red, slot, NS, ep);
+}
+
+// direct kernel with a multi-output epilogue (MODE 1, 2) at NS sites per tile
+template <typename K>
+void launch_epi(K k, const eofa_ctx* ctx, const Geom& g, int NS, size_t elem, bool hasop, int par, const void* in,
+                void* out, const void* gauge, const Op5& op, const void* y, double a_out, double b_in, double* red,
+                int slot, const Epi& ep, cudaStream_t st) {
+    const int threads = (NS * g.Ls + 31) / 32 * 32;
+    const size_t smem = hasop ? (size_t)NS * 12 * (g.Ls + 1) * elem : 0;
+    const int ntiles = (g.Vh + NS - 1) / NS;
+    if (smem > 40 * 1024) EOFA_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    unsigned grid = grid_size(k, threads, smem, ntiles, ctx->sms);
+    k<<<grid, threads, smem, st>>>(g, par, in, out, gauge, op, y, a_out, b_in, red, slot, NS, ep);
 }
 
 // Staged (bulk-copy) configurations are encoded as CFG_BULK | D << 8 | NS,
@@ -930,6 +1195,43 @@ void launch_dslash_t(const eofa_ctx* ctx, int par, const void* in, void* out, co
     EOFA_LAUNCHED();
 }
 
+// MODE 1 (second output, B = op) and MODE 2 (in-place update, B = identity)
+// use the direct kernel at the sites per tile that the autotuner picked for
+// the same hop shape (or the heuristic).
+template <int P, int DAG, int LS, int MODE>
+void launch_dslash_epi_t(const eofa_ctx* ctx, int par, const void* in, void* out, const Op5& op, const void* y,
+                         double a_out, double b_in, double* red, int slot, const Epi& ep, cudaStream_t st) {
+    typedef typename Field<P>::R R;
+    Geom g = ctx_geom(ctx);
+    const void* gauge = ctx->gauge[P == P64 ? P64 : P32];
+    constexpr bool HASOP = MODE == 1;
+    const long long key = ((((long long)P * 2 + DAG) * 128 + g.Ls) * 2 + (HASOP ? 1 : 0)) * 2 + (y ? 1 : 0);
+    int NS = pick_ns(g.Ls, sizeof(cpx<R>));
+    auto it = ctx->tuned->find(key);
+    if (it != ctx->tuned->end() && !(it->second & (CFG_BULK | CFG_PIPE))) NS = it->second / 4;
+    if (ctx->forced_cfg && !(ctx->forced_cfg & (CFG_BULK | CFG_PIPE))) NS = ctx->forced_cfg / 4;
+    if ((NS * g.Ls + 31) / 32 * 32 > 256) NS = pick_ns(g.Ls, sizeof(cpx<R>));
+    launch_epi(dslash_kernel<P, DAG, LS, HASOP, 1, MODE>, ctx, g, NS, sizeof(cpx<R>), HASOP, par, in, out, gauge, op,
+               y, a_out, b_in, red, slot, ep, st);
+    EOFA_LAUNCHED();
+}
+
+template <int P, int MODE>
+void dslash_epi_prec(const eofa_ctx* ctx, int par, int dag, const void* in, void* out, const Op5& op, const void* y,
+                     double a_out, double b_in, double* red, int slot, const Epi& ep, cudaStream_t st) {
+#define EPI_CASE(L)                                                                                      \
+    if (dag) launch_dslash_epi_t<P, 1, L, MODE>(ctx, par, in, out, op, y, a_out, b_in, red, slot, ep, st); \
+    else launch_dslash_epi_t<P, 0, L, MODE>(ctx, par, in, out, op, y, a_out, b_in, red, slot, ep, st);
+    switch (ctx->Ls) {
+        case 8: EPI_CASE(8) break;
+        case 12: EPI_CASE(12) break;
+        case 16: EPI_CASE(16) break;
+        case 24: EPI_CASE(24) break;
+        default: EPI_CASE(0) break;
+    }
+#undef EPI_CASE
+}
+
 template <int P, int LS>
 void launch_local5_t(const eofa_ctx* ctx, const Op5& op, const void* x, const void* z, double c0, const double* sc,
                      int it, int use_alpha, void* xw, void* out, double a_out, double* red, int slot, cudaStream_t st) {
@@ -997,7 +1299,13 @@ void xp_update_prec(const eofa_ctx* ctx, const double* sc, int it, void* x, void
                        const double* sc, int it, int use_alpha, void* xw, void* out, double a_out, double* red, \
                        int slot, cudaStream_t st);                                                              \
     void xp_update_##NAME(const eofa_ctx* ctx, const double* sc, int it, void* x, void* p, const void* s,      \
-                          cudaStream_t st);
+                          cudaStream_t st);                                                                     \
+    void dslash_to_##NAME(const eofa_ctx* ctx, int par, int dag, const void* in, void* out, const Op5& op,      \
+                          const void* y, double a_out, double b_in, double* red, int slot, const Op5& op2,      \
+                          void* out2, cudaStream_t st);                                                         \
+    void dslash_z_##NAME(const eofa_ctx* ctx, int par, int dag, const void* in, void* z, const Op5& op,         \
+                         const void* y, double a_out, double b_in, double* red, int slot, int it, void* r,      \
+                         int rslot, cudaStream_t st);
 DSL_DECLARE(p64)
 DSL_DECLARE(p32)
 DSL_DECLARE(p16)
@@ -1015,4 +1323,24 @@ DSL_DECLARE(p16)
     void xp_update_##NAME(const eofa_ctx* ctx, const double* sc, int it, void* x, void* p, const void* s,      \
                           cudaStream_t st) {                                                                    \
         dsl::xp_update_prec<P, PX>(ctx, sc, it, x, p, s, st);                                                   \
+    }                                                                                                           \
+    void dslash_to_##NAME(const eofa_ctx* ctx, int par, int dag, const void* in, void* out, const Op5& op,      \
+                          const void* y, double a_out, double b_in, double* red, int slot, const Op5& op2,      \
+                          void* out2, cudaStream_t st) {                                                        \
+        dsl::Epi ep;                                                                                            \
+        ep.op2 = op2;                                                                                           \
+        ep.out2 = out2;                                                                                         \
+        ep.it = 0;                                                                                              \
+        ep.slot2 = 0;                                                                                           \
+        dsl::dslash_epi_prec<P, 1>(ctx, par, dag, in, out, op, y, a_out, b_in, red, slot, ep, st);              \
+    }                                                                                                           \
+    void dslash_z_##NAME(const eofa_ctx* ctx, int par, int dag, const void* in, void* z, const Op5& op,         \
+                         const void* y, double a_out, double b_in, double* red, int slot, int it, void* r,      \
+                         int rslot, cudaStream_t st) {                                                          \
+        dsl::Epi ep;                                                                                            \
+        ep.op2 = op;                                                                                            \
+        ep.out2 = r;                                                                                            \
+        ep.it = it;                                                                                             \
+        ep.slot2 = rslot;                                                                                       \
+        dsl::dslash_epi_prec<P, 2>(ctx, par, dag, in, z, op, y, a_out, b_in, red, slot, ep, st);                \
     }

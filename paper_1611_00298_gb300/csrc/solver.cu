@@ -9,17 +9,26 @@
 // and the full residual is (0, G' (f^_o - A psi_o)).  A^+ follows from
 // D_hop^+ = gamma_5 D_hop gamma_5 and the reality of G' in s:
 //   A^+ = 1 - D^dag_oe G'^{-T} D^dag_eo G'^{-T}  (D^dag: hop with swapped projectors).
-// CGLS (CG on A^+ A tracking r = f^ - A x) iterates in the inner precision;
-// with mixed precision the residual is recomputed in FP64 whenever |r| has
+// CG on the normal equations A^+ A x = A^+ f^ (the least-squares form,
+// tracking r = f^ - A x and the normal residual s = A^+ r) iterates in the
+// inner precision with five fused launches per iteration (enqueue):
+//   te = G'^-1 D_eo p;  q = p - G'^-1 D_oe te, |q|^2 = delta, to = G'^-T q;
+//   te = G'^-T D^+_eo to;
+//   s <- s - alpha (q - D^+_oe te) = s - alpha A^+ q,  r <- r - alpha q,
+//   gamma' = |s|^2, |r|^2;  x += alpha p, p = s + beta p.
+// With mixed precision the residual is recomputed in FP64 whenever |r| has
 // dropped by the factor delta since the last recomputation (reliable
-// updates), and the solution accumulates in FP64.  The stopping test is the
-// FP64 true residual of the full, unpreconditioned system.
+// updates; they also reset s = A^+ r), and the solution accumulates in
+// FP64.  The stopping test is the FP64 true residual of the full,
+// unpreconditioned system.
 #include "solver.h"
 
 #include <algorithm>
 
 #include <chrono>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 
 namespace {
 
@@ -181,10 +190,42 @@ bool Solve::start_cg(cudaStream_t st) {
     return true;
 }
 
+// EOFA_CG=cgls selects the six-launch CG of the least-squares form, which
+// updates r itself (r -= alpha q) and forms s = A^+ r from it every
+// iteration, instead of the five-launch iteration on the normal residual.
+static bool use_cgls() {
+    static const int v = [] {
+        const char* e = getenv("EOFA_CG");
+        return (e && std::string(e) == "cgls") ? 1 : 0;
+    }();
+    return v != 0;
+}
+
+static bool solve_log() {
+    static const int v = getenv("EOFA_SOLVE_LOG") ? 1 : 0;
+    return v != 0;
+}
+
 void Solve::enqueue(int n, cudaStream_t st) {
+    if (use_cgls()) {
+        for (int k = 0; k < n; k++, it++) {
+            apply_A(ctx, Gi, prec, p, q, te, red, SC_DELTA, st);
+            apply_Adag_cg(ctx, GiT, prec, r, q, red, it, s, te, to, SC_RRH + (it % ring), SC_GAMMA + ((it + 1) & 1),
+                          st);
+            fused_xp_update(ctx, prec, precx, red, it, x, p, s, st);
+        }
+        inf.iters += n;
+        return;
+    }
     for (int k = 0; k < n; k++, it++) {
-        apply_A(ctx, Gi, prec, p, q, te, red, SC_DELTA, st);
-        apply_Adag_cg(ctx, GiT, prec, r, q, red, it, s, te, to, SC_RRH + (it % ring), SC_GAMMA + ((it + 1) & 1), st);
+        // q = A p, |q|^2 -> delta, to = G'^-T q
+        fused_dslash(ctx, prec, 0, 0, p, te, Gi, nullptr, 1.0, 0.0, nullptr, 0, st);
+        fused_dslash_to(ctx, prec, 1, 0, te, q, Gi, p, -1.0, 1.0, red, SC_DELTA, GiT, to, st);
+        // s -= alpha A^+ q, |s|^2 -> gamma (next parity); r -= alpha q, |r|^2 -> ring
+        fused_dslash(ctx, prec, 0, 1, to, te, GiT, nullptr, 1.0, 0.0, nullptr, 0, st);
+        fused_dslash_z(ctx, prec, 1, 1, te, s, op_identity(), q, -1.0, 1.0, red, SC_GAMMA + ((it + 1) & 1), it, r,
+                       SC_RRH + (it % ring), st);
+        // x += alpha p; p = s + beta p
         fused_xp_update(ctx, prec, precx, red, it, x, p, s, st);
     }
     inf.iters += n;
@@ -211,6 +252,9 @@ void Solve::check_value(double rr, cudaStream_t st) {
         blas_axpby(ctx, P64, 1.0, fh, -1.0, r64, st);
         rr = norm2_now(ctx, P64, r64, st);
         inf.reliable_updates++;
+        if (solve_log())
+            fprintf(stderr, "reliable update %d: iters %d, inner |r| %.3e, true |r| %.3e, last true %.3e, target %.3e\n",
+                    inf.reliable_updates, inf.iters, rn, std::sqrt(rr), rmax, target);
         rn = std::sqrt(rr);
         rmax = rn;
         if (rn < target || inf.iters >= P.maxiter) {

@@ -33,7 +33,7 @@ EXPORTS = [
     "eofa_dwf_apply_noalloc", "eofa_schur_hop_dev", "eofa_pseudofermion_solutions_dev",
     "eofa_set_reliable_delta", "eofa_leapfrog_dev", "eofa_rational_inv_sqrt", "eofa_heatbath_dev",
     "eofa_gauge_action_dev", "eofa_gauge_force_dev", "eofa_hmc_trajectory_dev", "eofa_force_parts_dev",
-    "eofa_check_device", "eofa_hmc_dev",
+    "eofa_check_device", "eofa_hmc_dev", "eofa_probe_fp64_fma",
 ]
 INT_LEAPFROG, INT_FG_PQPQP, INT_FG_QPQPQ = 0, 1, 2
 
@@ -144,6 +144,7 @@ def load_library(path: str = LIB_PATH):
         "eofa_heatbath_dev": (I, [P, I, D, D, D, D, I, D, I, D, P, P, P, P, I, ctypes.POINTER(SolveInfo), P]),
         "eofa_leapfrog_dev": (I, [P, I, D, D, D, D, I, D, I, D, P, P, P, ctypes.POINTER(D), ctypes.POINTER(D), P]),
         "eofa_hmc_dev": (I, [P, ctypes.POINTER(MDParams), I, D, I, P, P, P, P, P, P, ctypes.POINTER(HMCTrajInfo), P]),
+        "eofa_probe_fp64_fma": (I, [ctypes.POINTER(D)]),
         "eofa_profile_start": (I, [P]),
         "eofa_profile_stop": (I, [P, ctypes.POINTER(Profile)]),
     }
@@ -172,6 +173,15 @@ def _stream():
 def kernel_launches() -> int:
     """Number of CUDA kernels libeofa has launched since it was loaded."""
     return int(load_library().eofa_kernel_launches())
+
+
+def probe_fp64_fma() -> float:
+    """Measured FP64 FMA rate of the current GPU in TFLOP/s."""
+    v = ctypes.c_double()
+    rc = load_library().eofa_probe_fp64_fma(ctypes.byref(v))
+    if rc != OK:
+        raise EOFAError(rc, "eofa_probe_fp64_fma")
+    return v.value
 
 
 def rational_inv_sqrt(npoles, lmin, lmax):
