@@ -354,17 +354,22 @@ def hmc_chain_bench(args):
     t0 = time.perf_counter()
     th = lat.hmc_dev(Pth, None, uth, beta=beta, integrator=eofa.INT_FG_QPQPQ, nsteps=4, tau=1.0)
     t_therm = time.perf_counter() - t0
+    dHg = np.array([i["dH"] for i in th[n_therm // 2:]])
     del Pth
     a0, al, be, err = eofa.rational_inv_sqrt(12, 1e-3, 20.0)
     kw = dict(alpha=2.0, M5=1.8, m1=0.04, m2=1.0, precision=eofa.PREC_MIXED_F32, tol=1e-10, beta=beta,
               integrator=eofa.INT_FG_QPQPQ, nsteps=4, tau=1.0, n_inner=2)
 
     def draws(n, seed):
+        # momenta with density exp(-tr P^2); heatbath noise with density exp(-eta^+ eta), i.e. real and
+        # imaginary parts N(0, 1/2) (fermion4d draws N(0, 1) parts), so that phi = f(M) eta has density
+        # exp(-phi^+ M phi)
         Ps = torch.from_numpy(np.stack([inputs.momenta(dims, seed, stream=10 + k) for k in range(n)])).cuda()
-        etas = torch.from_numpy(np.stack([inputs.fermion4d(dims, seed + 1, stream=10 + k) for k in range(n)])).cuda()
+        etas = torch.from_numpy(np.stack([inputs.fermion4d(dims, seed + 1, stream=10 + k) for k in range(n)])
+                                / np.sqrt(2.0)).cuda()
         return Ps, etas, inputs.uniform(inputs.stream_key(seed + 2, 1), n)
     # the fermion changes the equilibrium: thermalise with it before measuring
-    n_therm_f = 24
+    n_therm_f = args.chain_therm
     t0 = time.perf_counter()
     thf = lat.hmc_dev(*draws(n_therm_f, 50), rational=(a0, al, be), **kw)
     t_therm_f = time.perf_counter() - t0
@@ -380,6 +385,9 @@ def hmc_chain_bench(args):
            "thermalisation": {"trajectories": n_therm, "acceptance": float(np.mean([i["accepted"] for i in th])),
                               "plaquette_end": th[-1]["plaquette"],
                               "plaquette_last_100_mean": float(np.mean([i["plaquette"] for i in th[-100:]])),
+                              "second_half_exp_minus_dH": float(np.exp(-dHg).mean()),
+                              "second_half_exp_minus_dH_err": float(np.exp(-dHg).std(ddof=1) / np.sqrt(len(dHg))),
+                              "second_half_dH_mean": float(dHg.mean()),
                               "seconds": round(t_therm, 2)},
            "thermalisation_with_eofa": {"trajectories": n_therm_f,
                                         "acceptance": float(np.mean([i["accepted"] for i in thf])),
@@ -389,6 +397,10 @@ def hmc_chain_bench(args):
            "exp_minus_dH_mean": float(e.mean()), "exp_minus_dH_err": float(e.std(ddof=1) / np.sqrt(len(e))),
            "dH_mean": float(dH.mean()), "dH_rms": float(np.sqrt(np.mean(dH ** 2))),
            "plaquette_mean": float(np.mean([i["plaquette"] for i in info])),
+           "plaquette_halves": [float(np.mean([i["plaquette"] for i in info[:n_traj // 2]])),
+                                float(np.mean([i["plaquette"] for i in info[n_traj // 2:]]))],
+           "plaquette_eofa_thermalisation_halves": [float(np.mean([i["plaquette"] for i in thf[:n_therm_f // 2]])),
+                                                    float(np.mean([i["plaquette"] for i in thf[n_therm_f // 2:]]))],
            "S_start_over_eta2": float(np.mean([i["S_eofa_start"] / i["eta_norm2"] for i in info])),
            "seconds_per_trajectory": round(t_chain / n_traj, 3),
            "solver_iters_per_trajectory": float(np.mean([i["solver_iters"] for i in info]))}
@@ -511,6 +523,7 @@ def main():
                     help="HMC chain at 8^4, Ls=8: pure-gauge thermalisation, then EOFA trajectories with heatbath "
                          "refresh and Metropolis; acceptance and <exp(-dH)>")
     ap.add_argument("--chain-traj", type=int, default=24)
+    ap.add_argument("--chain-therm", type=int, default=24, help="EOFA trajectories before the measured ones")
     ap.add_argument("--batched", action="store_true",
                     help="24 solves on three lattices (8^4x8, 12^4x12, 16^3x32x16): one batched, graph-captured "
                          "mixed-precision call vs sequential FP64 solves")

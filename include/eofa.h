@@ -305,9 +305,12 @@ int eofa_hmc_trajectory_dev(eofa_ctx* ctx, const eofa_md_params* p, const double
  * The context's links are the chain's state: they start as loaded and end
  * at the last accepted configuration (copied to U_dev, canonical, if not
  * NULL).  All random numbers are inputs: P_dev holds ntraj momentum fields
- * (each 4 V traceless Hermitian 3x3, canonical, device), eta_dev ntraj 4D
- * Gaussian fields (device; may be NULL when npoles = 0), u ntraj uniforms
- * in [0, 1) (host).  info[k] gets trajectory k's record.  EOFA_EINVAL for
+ * (each 4 V traceless Hermitian 3x3, canonical, device) drawn with density
+ * exp(-tr P^2) (P = sum_a p_a T^a, p_a ~ N(0, 1)); eta_dev ntraj 4D Gaussian
+ * fields with density exp(-eta^+ eta), i.e. real and imaginary parts
+ * N(0, 1/2) (device; may be NULL when npoles = 0), so that phi has density
+ * exp(-phi^+ M_EOFA phi); u ntraj uniforms in [0, 1) (host).  Draws from
+ * other distributions give a chain that does not sample exp(-H).  info[k] gets trajectory k's record.  EOFA_EINVAL for
  * bad arguments; a failed solve or trajectory stops the chain with its
  * status (info holds the records of the trajectories before it). */
 typedef struct {

@@ -219,7 +219,8 @@ def hmc_chain(U, Ps, us, beta, tau, nsteps, scheme="qpqpq", n_inner=0, fermion=N
     """HMC Markov chain of len(us) trajectories.
 
     Trajectory k: when ``fermion`` is given (dict(Ls, alpha, M5, m1, m2, bc_t,
-    tol)), a fresh pseudofermion phi = f(M_EOFA) eta_k from the heatbath of
+    tol)), a fresh pseudofermion phi = f(M_EOFA) eta_k (eta_k with density
+    exp(-eta^+ eta): real and imaginary parts N(0, 1/2)) from the heatbath of
     Eq. (6) with f(x) = alpha0 + sum_l alphas[l] / (x + betas[l]) (rational =
     (alpha0, alphas, betas)); the MD trajectory of H = sum tr P^2 + S_g +
     S_EOFA(phi) from momenta Ps[k] (``trajectory``); the Metropolis step with

@@ -3,8 +3,9 @@
 // the force 2 (Sec. 3.2, 3.3, 5.2); the mass pairs of several EOFA factors
 // add more.
 //
-// Systems on the same lattice and with the same inner precision form a
-// group (at most MR_MAX systems).  A group iterates its systems in lock
+// Systems on the same (small) lattice and with the same inner precision
+// form a group (at most MR_MAX systems); a system on a large lattice is a
+// group of its own (MR_SINGLE_SITES).  A group iterates its systems in lock
 // step with the multi-system kernels of mrhs.cuh: the five launches of the
 // CG iteration of solver.cu, each for all of them, each link row and
 // neighbour index fetched once for the whole group.  The CG loop of a group runs on the device: a CUDA graph
@@ -27,6 +28,14 @@
 #include <map>
 #include <memory>
 #include <thread>
+
+// Systems on lattices of at least this many 5D sites per checkerboard run
+// as groups of one, with the single-system (autotuned) kernels of
+// solver.cu inside the same device loop: there a system alone fills the GPU
+// and shares too few bytes (the links are 576/Ls of 192 + 576/Ls per site in
+// FP32) for lock step to pay (measured at 16^3 x 32 x 16: 8 systems took
+// 3.31 s in one group, 2.98 s one after another).
+#define MR_SINGLE_SITES (1LL << 19)
 
 // CG iterations per loop body; the residual ring of every batched system
 // has this length, so the ring slots and CG-scalar parities baked into the
@@ -91,6 +100,9 @@ struct Group {
     Op5* ops = nullptr;          // device: [Gi x MR_MAX][GiT x MR_MAX] of the captured set
     double* ctl = nullptr;       // device control block
     double* ctl_host = nullptr;  // pinned mirror
+    bool single = false;          // one system, single-system kernels
+    bool eager_done = false;      // single: the first chunk ran outside a graph (autotuning)
+    std::vector<int> last;        // systems of the last launch (graph or eager chunk)
     bool running = false;
     bool finished = false;
     // diagnostics (EOFA_BATCH_LOG=1): host visits, graph builds, host seconds
@@ -163,7 +175,17 @@ void build_graph(Group& g, std::vector<Solve>& sv, const std::vector<int>& activ
     if (g.ctx->prof) g.ctx->prof->on = false;  // no event records inside a conditional body
     try {
         EOFA_CUDA(cudaStreamBeginCaptureToGraph(g.st, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-        for (int it = 0; it < MR_BODY; it++) enqueue_group_iteration(g, sv, it, g.st);
+        if (g.single) {
+            // the single-system launches of Solve::enqueue; the counters it advances
+            // are put back (collect_group adds the iterations the loop ran)
+            Solve& s1 = sv[active[0]];
+            const int it0 = s1.it, n0 = s1.inf.iters;
+            s1.enqueue(MR_BODY, g.st);
+            s1.it = it0;
+            s1.inf.iters = n0;
+        } else {
+            for (int it = 0; it < MR_BODY; it++) enqueue_group_iteration(g, sv, it, g.st);
+        }
         MRPtrs d = {};
         for (int a = 0; a < n; a++) d.red[a] = sv[active[a]].red;
         mr_decide_kernel<<<1, 32, 0, g.st>>>(d, n, g.ctl, handle);
@@ -210,7 +232,20 @@ bool service_group(Group& g, std::vector<Solve>& sv, std::vector<bool>& finished
             if (!finished[i]) throw eofa_error(EOFA_EDEVICE, "batched solve: a system neither finished nor active");
         return false;
     }
-    if (active != g.captured) build_graph(g, sv, active);
+    g.last = active;
+    if (g.single && !g.eager_done) {
+        // first chunk outside a graph, so that the autotuner can time the kernel
+        // shapes (it does not run during stream capture)
+        Solve& s1 = sv[active[0]];
+        s1.enqueue(MR_BODY, g.st);
+        g.eager_done = true;
+        g.ctl_host[CTL_ITERS] = 0.0;  // enqueue advanced the counters itself
+        EOFA_CUDA(cudaMemcpyAsync(g.ctl_host + CTL_RR, s1.last_rr(), sizeof(double), cudaMemcpyDeviceToHost, g.st));
+        EOFA_CUDA(cudaEventRecord(g.done, g.st));
+        g.running = true;
+        return true;
+    }
+    if (!g.exec || active != g.captured) build_graph(g, sv, active);
     for (size_t a = 0; a < active.size(); a++) {
         const Solve& s = sv[active[a]];
         const double thr = s.mixed ? std::max(s.delta * s.rmax, s.target) : s.target;
@@ -233,8 +268,8 @@ bool service_group(Group& g, std::vector<Solve>& sv, std::vector<bool>& finished
 void collect_group(Group& g, std::vector<Solve>& sv) {
     g.running = false;
     const int n = (int)std::lround(g.ctl_host[CTL_ITERS]);
-    for (size_t a = 0; a < g.captured.size(); a++) {
-        Solve& s = sv[g.captured[a]];
+    for (size_t a = 0; a < g.last.size(); a++) {
+        Solve& s = sv[g.last[a]];
         s.it += n;
         s.inf.iters += n;
         s.check_value(g.ctl_host[CTL_RR + a], g.st);
@@ -265,12 +300,14 @@ extern "C" int eofa_solve_batched(eofa_ctx* const* ctxs, int n, const eofa_solve
                                  ? P64
                                  : (params[i].precision == EOFA_PREC_MIXED_F16 ? P16 : P32);
             auto key = std::make_pair(ctxs[i], prec);
-            Group* g = open.count(key) ? open[key] : nullptr;
+            const bool single = (long long)ctxs[i]->Vh * ctxs[i]->Ls >= MR_SINGLE_SITES;
+            Group* g = (!single && open.count(key)) ? open[key] : nullptr;
             if (!g || (int)g->members.size() >= MR_MAX) {
                 groups.emplace_back(new Group());
                 g = groups.back().get();
                 g->ctx = ctxs[i];
                 g->prec = prec;
+                g->single = single;
                 EOFA_CUDA(cudaStreamCreateWithFlags(&g->st, cudaStreamNonBlocking));
                 EOFA_CUDA(cudaEventCreateWithFlags(&g->done, cudaEventDisableTiming));
                 const std::string gt = "_g" + std::to_string(groups.size() - 1);

@@ -187,9 +187,18 @@ __device__ __forceinline__ void hop_mu(const Geom& g, int par, int j, const int*
 #pragma unroll
         for (int k = 0; k < SPT; k++) {
             cpx<R> psi[12];
-            Field<P>::load(in, jn, sv[k], Ls, n5, psi);
-            if (dirn == 0) project<MU, DAG ? 1 : -1>(psi, h[k]);
-            else project<MU, DAG ? -1 : 1>(psi, h[k]);
+            if constexpr (P == P16) {
+                // project the stored unit-scale values, then scale the 6 components of h
+                const float sc = Field<P16>::load_unscaled(in, jn, sv[k], Ls, n5, psi);
+                if (dirn == 0) project<MU, DAG ? 1 : -1>(psi, h[k]);
+                else project<MU, DAG ? -1 : 1>(psi, h[k]);
+#pragma unroll
+                for (int c = 0; c < 6; c++) h[k][c] = sc * h[k][c];
+            } else {
+                Field<P>::load(in, jn, sv[k], Ls, n5, psi);
+                if (dirn == 0) project<MU, DAG ? 1 : -1>(psi, h[k]);
+                else project<MU, DAG ? -1 : 1>(psi, h[k]);
+            }
         }
         const long long lidx = dirn == 0 ? (long long)((par * 4 + MU) * g.Vh + j)
                                          : (long long)(((1 - par) * 4 + MU) * g.Vh + jn);
@@ -437,140 +446,9 @@ __device__ __forceinline__ void column_op(const Op5& op, int c, cpx<R>* col, int
     }
 }
 
-// 1: at Ls >= 16 (even) two neighbouring lanes share each FP32 column of
-// the 5D-local block, each running the recurrences over half of s
-#ifndef EOFA_COL_SPLIT
-#define EOFA_COL_SPLIT 0
-#endif
-
-__device__ __forceinline__ f2p shfl_pair(f2p v) { return __shfl_xor_sync(0xffffffffu, v, 1); }
-__device__ __forceinline__ f2p add_pair(f2p v) {
-    f2p r;
-    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(v), "l"(shfl_pair(v)));
-    return r;
-}
-
-// Streaming form of the block (as col_stream_f2) on one FP32 column by a
-// lane pair: lane half = 0 takes t in [0, Lh), half = 1 takes [Lh, Ls) in the
-// recurrence's own order t (t = s for the down-shift, Ls - 1 - s for the
-// up-shift).  The corner sum is split and joined with mr^Lh; the inverse
-// recurrence u_t = invp x_t + mr u_{t-1} runs in both halves at once, the
-// upper half from zero, then adds mr^(t - Lh + 1) u_{Lh-1}; the last values
-// of each half cross by one shuffle.  Every lane of the warp calls this (act
-// = false: a lane pair without a column computes on column 0 and writes
-// nothing), so the shuffles see full warps.
-template <int LS, bool R1>
-__device__ __forceinline__ void col_split_f2(const Half<float>& H, cpx<float>* col, int half, bool act) {
-    constexpr int LH = LS / 2;
-    const int dir = H.dir1;
-    auto at = [&](int t) { return dir == 0 ? t : LS - 1 - t; };
-    const f2p MR = splat2(H.mr), INVP = splat2(H.invp);
-    const float p2 = H.fwd ? H.p2 : 1.f, q2 = H.fwd ? H.q2 : 0.f;
-    const f2p P2 = splat2(p2), Q2 = splat2(q2), Q2M = splat2(-q2 * H.mass);
-    const int t0 = half ? LH : 0;
-    // corner sum: sum_{t>=1} mr^(Ls-t) x_t = mr^Lh A0 + A1
-    f2p acc = 0ull;
-#pragma unroll
-    for (int k = 0; k < LH; k++) {
-        const int t = t0 + k;
-        if (t >= 1) acc = fma2(MR, acc, ld2(col + at(t)));
-    }
-    acc = mul2(MR, acc);
-    float mrh = 1.f;
-#pragma unroll
-    for (int k = 0; k < LH; k++) mrh *= H.mr;
-    const f2p other = shfl_pair(acc);
-    const f2p total = half ? fma2(splat2(mrh), other, acc) : fma2(splat2(mrh), acc, other);
-    // inverse recurrence; the lower half starts from u_0, the upper from zero
-    f2p u;
-    if (half == 0) {
-        u = mul2(splat2(H.invN), fma2(splat2(-H.mass), total, ld2(col + at(0))));
-        if (act) st2(col + at(0), u);
-    } else {
-        u = 0ull;
-    }
-#pragma unroll
-    for (int k = (half == 0 ? 1 : 0); k < LH; k++) {
-        const int t = t0 + k;
-        u = fma2(MR, u, mul2(INVP, ld2(col + at(t))));
-        if (act) st2(col + at(t), u);
-    }
-    // u_{Lh-1} to the upper half, which adds mr^(t - Lh + 1) u_{Lh-1}
-    const f2p ulow = shfl_pair(u);
-    f2p d = 0ull;
-    if (half == 1) {
-        f2p pw = MR;
-#pragma unroll
-        for (int k = 0; k < LH; k++) {
-            const int t = LH + k;
-            const f2p v = fma2(pw, ulow, ld2(col + at(t)));
-            if (act) st2(col + at(t), v);
-            if (R1) d = fma2(splat2(H.v[at(t)]), v, d);
-            pw = mul2(pw, MR);
-        }
-    } else if (R1) {
-#pragma unroll
-        for (int k = 0; k < LH; k++) d = fma2(splat2(H.v[at(k)]), ld2(col + at(k)), d);
-    }
-    // u_{Ls-1} from the upper half (its last value after the fix-up)
-    const f2p ulast_up = half == 1 ? ld2(col + at(LS - 1)) : 0ull;
-    const f2p ulast = shfl_pair(ulast_up);
-    const f2p uprev_low = shfl_pair(u);  // the lower half's u_{Lh-1} for the upper half's first output
-    // out_t = p2 u_t + q2 u_{t-1}, out_0 = p2 u_0 - q2 mass u_{Ls-1}; downwards so that u_{t-1} is still there
-#pragma unroll
-    for (int k = LH - 1; k >= 0; k--) {
-        const int t = t0 + k;
-        const f2p ut = ld2(col + at(t));
-        f2p o;
-        if (t == 0) o = fma2(P2, ut, mul2(Q2M, ulast));
-        else if (k == 0) o = fma2(P2, ut, mul2(Q2, uprev_low));
-        else o = fma2(P2, ut, mul2(Q2, ld2(col + at(t - 1))));
-        if (act) st2(col + at(t), o);
-    }
-    if (R1) {
-        // rank-one term: out += sigma w (v . u), v . u summed over both halves
-        d = mul2(splat2(H.sigma), add_pair(d));
-#pragma unroll
-        for (int k = 0; k < LH; k++) {
-            const int t = t0 + k;
-            if (act) st2(col + at(t), fma2(splat2(H.w[at(t)]), d, ld2(col + at(t))));
-        }
-    }
-}
-
-// Lane-pair form of the column loop of a tile: every lane takes part.
-template <int LS>
-__device__ __forceinline__ void columns_split_f2(const Op5& op, cpx<float>* sm, int ncols, int LsP, const float* wv) {
-    const int per = blockDim.x >> 1;
-    const int half = threadIdx.x & 1;
-    for (int base = 0; base < ncols; base += per) {
-        const int idx = base + (threadIdx.x >> 1);
-        const bool act = idx < ncols;
-        const int c = act ? idx % 12 : 0;
-        const Half<float> H = half_of<float>(op, c < 6 ? 0 : 1, wv, LS);
-        cpx<float>* col = sm + (act ? idx : 0) * LsP;
-        if (H.sigma == 0.f) col_split_f2<LS, false>(H, col, half, act);
-        else col_split_f2<LS, true>(H, col, half, act);
-    }
-}
-
-// whether the lane-pair column form applies to this block (every column
-// uses the streaming form of col_stream)
-__device__ __forceinline__ bool split_ok(const Op5& op) {
-    for (int h = 0; h < 2; h++)
-        if (!op.inv[h] || (op.fwd[h] && op.dir2[h] != op.dir1[h])) return false;
-    return true;
-}
-
-// the column phase of a tile: lane pairs where they apply, one lane per column otherwise
+// the column phase of a tile: one thread per (site, component) column
 template <typename R, int LS>
 __device__ __forceinline__ void columns(const Op5& op, cpx<R>* sm, int ncols, int LsP, int Ls, const R* wv) {
-    if constexpr (EOFA_COL_SPLIT && std::is_same<R, float>::value && LS >= 16 && LS % 2 == 0) {
-        if (split_ok(op)) {
-            columns_split_f2<LS>(op, sm, ncols, LsP, wv);
-            return;
-        }
-    }
     for (int idx = threadIdx.x; idx < ncols; idx += blockDim.x) column_op<R, LS>(op, idx % 12, sm + idx * LsP, Ls, wv);
 }
 

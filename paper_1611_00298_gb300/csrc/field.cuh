@@ -106,6 +106,25 @@ struct Field<P16> {
             }
         }
     }
+    // the stored (unit-scale) values and the site's scale, for callers that
+    // apply the scale after a linear step (the hop scales its half spinors)
+    static __device__ __forceinline__ float load_unscaled(const void* base, int j, int s, int Ls, long long n5,
+                                                          cpx<float> v[12]) {
+        const uint4* b = (const uint4*)base + (long long)j * 3 * Ls + s;
+        const float sc = __ldg(scales(base, n5) + (long long)j * Ls + s);
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            uint4 t = __ldg(b + k * Ls);
+            unsigned w[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+            for (int e = 0; e < 4; e++) {
+                __half2 h = *reinterpret_cast<__half2*>(&w[e]);
+                float2 f = __half22float2(h);
+                v[4 * k + e] = mk(f.x, f.y);
+            }
+        }
+        return sc;
+    }
     static __device__ __forceinline__ void store(void* base, int j, int s, int Ls, long long n5,
                                                  const cpx<float> v[12]) {
         float m = 0.f;

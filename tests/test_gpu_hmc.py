@@ -224,7 +224,7 @@ def test_hmc_chain_matches_oracle_chain(eofa):
     dims, Ls, ntraj = (2, 2, 2, 2), 4, 4
     U0 = inputs.gauge_field(dims, 0.4, 31)
     Ps = [inputs.momenta(dims, 32, stream=10 + k) for k in range(ntraj)]
-    etas = [inputs.fermion4d(dims, 33, stream=20 + k) for k in range(ntraj)]
+    etas = [inputs.fermion4d(dims, 33, stream=20 + k) / np.sqrt(2.0) for k in range(ntraj)]  # density exp(-eta^+ eta)
     us = inputs.uniform(inputs.stream_key(34, 1), ntraj)
     rational = _rational_fit(10, 1e-2, 10.0)
     fermion = dict(Ls=Ls, alpha=ALPHA, M5=M5, m1=M1, m2=M2, bc_t=-1.0, tol=1e-13)

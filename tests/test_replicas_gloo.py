@@ -32,7 +32,8 @@ def test_two_gloo_ranks_aggregate_like_the_bench():
     torch = pytest.importorskip("torch")
     import torch.multiprocessing as mp
     world, port = 2, _free_port()
-    with mp.Manager() as m:
+    # spawn, not fork: the test process may already run OpenMP threads (C oracle)
+    with mp.get_context("spawn").Manager() as m:
         out = m.dict()
         mp.spawn(_rank, args=(world, port, out), nprocs=world, join=True)
         res = dict(out)
