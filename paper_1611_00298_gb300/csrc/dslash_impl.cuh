@@ -302,8 +302,10 @@ __device__ __forceinline__ Half<R> half_of(const Op5& op, int h, const R* wv, in
 // Streaming form of B for a compile-time Ls when the inverse and the matrix
 // use the same shift direction (every block built in ops.cu): one pass for
 // the Horner sum of the corner term, one pass that runs the inverse
-// recurrence u_s and emits (p2 + q2 L) u on the fly; two live values per
-// step instead of the whole column.
+// recurrence u_s = mr u_{s-1} + x_s / p (mr = -q / p; x_s / p does not
+// wait for u, so one multiply-add per step is on the dependent chain) and
+// emits (p2 + q2 L) u on the fly; two live values per step instead of the
+// whole column.
 template <typename R>
 struct Vec2;
 template <>
@@ -331,7 +333,7 @@ __device__ __forceinline__ void sts(cpx<R>* p, cpx<R> a) {
 
 template <typename R, int LS, bool R1>
 __device__ __forceinline__ void col_stream(const Half<R>& H, cpx<R>* col) {
-    const R q = H.q1, mass = H.mass, mr = H.mr, invp = H.invp, invN = H.invN;
+    const R mass = H.mass, mr = H.mr, invp = H.invp, invN = H.invN;
     const R p2 = H.fwd ? H.p2 : R(1), q2 = H.fwd ? H.q2 : R(0);
     cpx<R> acc = mk(R(0), R(0)), d = mk(R(0), R(0));
     if (H.dir1 == 0) {
@@ -343,7 +345,7 @@ __device__ __forceinline__ void col_stream(const Half<R>& H, cpx<R>* col) {
         if (R1) d = H.v[0] * u0;
 #pragma unroll
         for (int s = 1; s < LS; s++) {
-            const cpx<R> un = invp * (lds(col + s) - q * u);
+            const cpx<R> un = mr * u + invp * lds(col + s);
             if (R1) d = d + H.v[s] * un;
             sts(col + s, p2 * un + q2 * u);
             u = un;
@@ -358,7 +360,7 @@ __device__ __forceinline__ void col_stream(const Half<R>& H, cpx<R>* col) {
         if (R1) d = H.v[LS - 1] * uL;
 #pragma unroll
         for (int s = LS - 2; s >= 0; s--) {
-            const cpx<R> un = invp * (lds(col + s) - q * u);
+            const cpx<R> un = mr * u + invp * lds(col + s);
             if (R1) d = d + H.v[s] * un;
             sts(col + s, p2 * un + q2 * u);
             u = un;
@@ -378,8 +380,7 @@ __device__ __forceinline__ void col_stream(const Half<R>& H, cpx<R>* col) {
 // each complex multiply-add is one f32x2 instruction.
 template <int LS, bool R1>
 __device__ __forceinline__ void col_stream_f2(const Half<float>& H, cpx<float>* col) {
-    const f2p MR = splat2(H.mr), NM = splat2(-H.mass), INVN = splat2(H.invN), NQ = splat2(-H.q1),
-              INVP = splat2(H.invp);
+    const f2p MR = splat2(H.mr), NM = splat2(-H.mass), INVN = splat2(H.invN), INVP = splat2(H.invp);
     const float p2 = H.fwd ? H.p2 : 1.f, q2 = H.fwd ? H.q2 : 0.f;
     const f2p P2 = splat2(p2), Q2 = splat2(q2), Q2M = splat2(-q2 * H.mass);
     f2p acc = 0ull, d = 0ull;
@@ -392,7 +393,7 @@ __device__ __forceinline__ void col_stream_f2(const Half<float>& H, cpx<float>* 
         if (R1) d = mul2(splat2(H.v[0]), u0);
 #pragma unroll
         for (int s = 1; s < LS; s++) {
-            const f2p un = mul2(INVP, fma2(NQ, u, ld2(col + s)));
+            const f2p un = fma2(MR, u, mul2(INVP, ld2(col + s)));
             if (R1) d = fma2(splat2(H.v[s]), un, d);
             st2(col + s, fma2(P2, un, mul2(Q2, u)));
             u = un;
@@ -407,7 +408,7 @@ __device__ __forceinline__ void col_stream_f2(const Half<float>& H, cpx<float>* 
         if (R1) d = mul2(splat2(H.v[LS - 1]), uL);
 #pragma unroll
         for (int s = LS - 2; s >= 0; s--) {
-            const f2p un = mul2(INVP, fma2(NQ, u, ld2(col + s)));
+            const f2p un = fma2(MR, u, mul2(INVP, ld2(col + s)));
             if (R1) d = fma2(splat2(H.v[s]), un, d);
             st2(col + s, fma2(P2, un, mul2(Q2, u)));
             u = un;

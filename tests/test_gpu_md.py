@@ -100,6 +100,48 @@ def test_force_sampled_links_16I_shape(eofa, alpha):
     lat.close()
 
 
+@pytest.mark.parametrize("alpha", [1.0, 2.0])
+def test_force_central_differences_16I_shape(eofa, alpha):
+    """16^3 x 32, Ls = 12, Shamir (alpha = 1) and Moebius (alpha = 2): the GPU
+    force F^a (Eq. (7)) at 16 (link, generator) pairs against central
+    differences (delta = 1e-5) of the GPU action (Eq. (5)).  phi is Gaussian on
+    one 2^4 block (at the time boundary) and zero elsewhere, so that S is of
+    order ten and its change 2 delta F^a is resolved by solves to 1e-12
+    (with phi Gaussian everywhere S ~ 3e6 would need 1e-14 accuracy); the
+    solves still span the whole lattice.  The pairs sit on and next to the
+    block, some on the antiperiodic t-boundary links."""
+    dims, Ls = (16, 16, 16, 32), 12
+    U = inputs.gauge_field(dims, 0.5, 4)
+    full = inputs.fermion4d(dims, 4)
+    phi = np.zeros_like(full)
+    blk = (slice(30, 32), slice(6, 8), slice(6, 8), slice(6, 8))
+    phi[blk] = full[blk]
+    lat = eofa.Lattice(dims, Ls)
+    lat.gauge_load(U)
+    kw = dict(alpha=alpha, M5=M5, m1=M1, m2=M2, precision=eofa.PREC_MIXED_F32, tol=1e-12)
+    F, S0, info = lat.force(phi, **kw)
+    assert info[0].true_resid <= 1e-12 and info[1].true_resid <= 1e-12
+    Fa = oeofa.force_components(F)
+    rng = np.random.default_rng(11)
+    d = 1e-5
+    worst = 0.0
+    for n in range(16):
+        site = (int(rng.integers(29, 32)), int(rng.integers(5, 9)), int(rng.integers(5, 9)), int(rng.integers(5, 9)))
+        mu = 3 if n < 4 else int(rng.integers(4))  # the first four on t-links, some across the boundary
+        a = int(rng.integers(8))
+        vals = []
+        for w in (d, -d):
+            lat.gauge_load(_perturb(U, site, mu, a, w))
+            vals.append(lat.action(phi, **kw)[0])
+        fd = (vals[0] - vals[1]) / (2 * d)
+        ref = Fa[site + (mu, a)]
+        err = abs(fd - ref)
+        worst = max(worst, err / max(1.0, abs(ref)))
+        assert err < 1e-5 * max(1.0, abs(ref)) + 1e-6, (site, mu, a, fd, ref)
+    assert np.abs(Fa).max() > 1e-2  # the sampled region carries a force
+    lat.close()
+
+
 def test_leapfrog_matches_oracle(eofa):
     import torch
     dims, Ls = (2, 2, 2, 2), 4

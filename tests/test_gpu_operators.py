@@ -295,3 +295,10 @@ def test_variant_kernels_every_ls(eofa, cfg, Ls, monkeypatch):
                 assert _rel(res.cpu().numpy(), ref) < tol, (cfg, Ls, prec, out_par, dag)
     lat.check_device()
     lat.close()
+
+
+def test_fp64_fma_probe_reports_a_plausible_rate(eofa):
+    """eofa_probe_fp64_fma: a positive, finite FP64 rate below GB300's nominal FP64
+    vector rate of ~1.3 TFLOP/s with headroom (it is a denominator of the FP64 hop)."""
+    v = eofa.probe_fp64_fma()
+    assert 0.05 < v < 5.0, v
