@@ -74,7 +74,7 @@ typedef struct {
     double tol;       /* target true relative residual |b - A x| / |b| */
     int maxiter;      /* cap on inner iterations (all restarts) */
     double delta;     /* reliable-update threshold (mixed precision); <= 0: default
-                         (1e-3 for FP32 inner storage, 0.1 for FP16, which is
+                         (1e-4 for FP32 inner storage, 0.1 for FP16, which is
                          never below 0.05) */
     int use_x0;       /* 1: x holds the initial guess on entry */
 } eofa_solve_params;

@@ -70,11 +70,26 @@ void fused_dslash_z(const eofa_ctx* ctx, int prec, int out_parity, int dagger, c
                     cudaStream_t st) {
     const Op5 opf = op_finalize(op, ctx->Ls);
     const double n5h = (double)ctx->Vh * ctx->Ls;
-    // in, y, z and r read, z and r written
-    const double bytes = n5h * spinor_bytes(prec) * 6.0 + 8.0 * ctx->Vh * (prec == P64 ? 144.0 : 72.0);
+    // in, y and z read, z written; r read and written when given
+    const double bytes = n5h * spinor_bytes(prec) * (r ? 6.0 : 4.0) + 8.0 * ctx->Vh * (prec == P64 ? 144.0 : 72.0);
     prof_begin(ctx, prec, st, bytes);
     if (prec == P64) dslash_z_p64(ctx, out_parity, dagger, in, z, opf, y, a_out, b_in, red, slot, it, r, rslot, st);
     else if (prec == P32) dslash_z_p32(ctx, out_parity, dagger, in, z, opf, y, a_out, b_in, red, slot, it, r, rslot, st);
     else dslash_z_p16(ctx, out_parity, dagger, in, z, opf, y, a_out, b_in, red, slot, it, r, rslot, st);
+    prof_end(ctx, st);
+}
+
+void fused_dslash_x(const eofa_ctx* ctx, int prec, int out_parity, int dagger, const void* in, void* out,
+                    const Op5& op, double* red, int it, void* x, const void* p, void* r, const void* q, int rslot,
+                    cudaStream_t st) {
+    const Op5 opf = op_finalize(op, ctx->Ls);
+    const double n5h = (double)ctx->Vh * ctx->Ls;
+    // in, out; p, q read; x and r read and written (x in FP32 when the field is FP16)
+    const double xb = prec == P16 ? 96.0 : spinor_bytes(prec);
+    const double bytes = n5h * (spinor_bytes(prec) * 6.0 + 2.0 * xb) + 8.0 * ctx->Vh * (prec == P64 ? 144.0 : 72.0);
+    prof_begin(ctx, prec, st, bytes);
+    if (prec == P64) dslash_x_p64(ctx, out_parity, dagger, in, out, opf, red, it, x, p, r, q, rslot, st);
+    else if (prec == P32) dslash_x_p32(ctx, out_parity, dagger, in, out, opf, red, it, x, p, r, q, rslot, st);
+    else dslash_x_p16(ctx, out_parity, dagger, in, out, opf, red, it, x, p, r, q, rslot, st);
     prof_end(ctx, st);
 }

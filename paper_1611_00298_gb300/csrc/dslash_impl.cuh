@@ -574,9 +574,13 @@ __device__ __forceinline__ double cg_beta(const double* sc, int it) {
 
 // Extra epilogue of the CG launches with more than one output (MODE 1, 2).
 struct Epi {
-    Op5 op2;        // MODE 1: block of the second output
-    void* out2;     // MODE 1: out2 = B2 out;  MODE 2: r, updated in place (r -= alpha y)
-    int it, slot2;  // MODE 2: iteration of the CG scalars, slot of |r|^2
+    Op5 op2;           // MODE 1: block of the second output
+    void* out2;        // MODE 1: out2 = B2 out;  MODE 2: r (may be null), updated in place (r -= alpha y);
+                       // MODE 3: x, updated in place (x += alpha aux)
+    const void* aux;   // MODE 3: p
+    void* out3;        // MODE 3: r, updated in place (r -= alpha aux2)
+    const void* aux2;  // MODE 3: q
+    int it, slot2;     // MODE 2, 3: iteration of the CG scalars and the slot of |r|^2
 };
 
 // HASOP = false: B is the identity (plain hop), compiled separately so that
@@ -584,7 +588,11 @@ struct Epi {
 // MODE 0: out = value.  MODE 1: also out2 = B2 out (a second 5D-local pass
 // through shared memory).  MODE 2: out is updated in place,
 // out <- out - alpha(red, it) value, and so is out2 <- out2 - alpha y, with
-// |out|^2 -> red[slot] and |out2|^2 -> red[ep.slot2].
+// |out|^2 -> red[slot] and |out2|^2 -> red[ep.slot2] (out2 may be null).
+// MODE 3: out = value, and the CG updates x <- x + alpha(red, it) p and
+// r <- r - alpha q at the same (j, s), |r|^2 -> red[ep.slot2] (x = out2 in
+// the solution's precision, p = aux, r = out3, q = aux2): elementwise
+// updates ride in this latency-bound launch instead of streaming kernels.
 // SPT slices per thread: thread (site, sh) handles s = sh + k Ls/SPT,
 // k < SPT, so neighbour indices and link rows are loaded once for SPT output
 // sites (Ls/SPT threads per site; SPT = 2 needs an even Ls).
@@ -609,6 +617,10 @@ __global__ void __launch_bounds__(256, SPT == 2 ? 2 : (MODE == 1 ? EOFA_MODE1_MI
     if (MODE == 1) stage_wv<R>(ep.op2, Ls, wv2_s);
     if (HASOP || MODE == 1) __syncthreads();
     const R cz = MODE == 2 ? (R)(-cg_alpha(red, ep.it)) : R(0);
+    // MODE 3: x is stored in FP32 when the field is FP16, else in the field's precision
+    constexpr int PX = P == P16 ? P32 : P;
+    typedef typename Field<PX>::R RX;
+    const RX ax = MODE == 3 ? (RX)cg_alpha(red, ep.it) : RX(0);
     const long long n5 = (long long)g.Vh * Ls;
     const int ls = threadIdx.x / Lt, sh = threadIdx.x - ls * Lt;
     int sv[SPT];
@@ -670,7 +682,7 @@ __global__ void __launch_bounds__(256, SPT == 2 ? 2 : (MODE == 1 ? EOFA_MODE1_MI
                     const R bb = (R)b_in;
 #pragma unroll
                     for (int c = 0; c < 12; c++) acc[k][c] = acc[k][c] + bb * yv[c];
-                    if (MODE == 2) {
+                    if (MODE == 2 && ep.out2 != nullptr) {
                         // r <- r - alpha y
                         cpx<R> rv[12];
                         Field<P>::load_stream(ep.out2, j, sv[k], Ls, n5, rv);
@@ -688,7 +700,27 @@ __global__ void __launch_bounds__(256, SPT == 2 ? 2 : (MODE == 1 ? EOFA_MODE1_MI
                 }
                 if (EOFA_STREAM_HINTS) Field<P>::store_stream(out, j, sv[k], Ls, n5, acc[k]);
                 else Field<P>::store(out, j, sv[k], Ls, n5, acc[k]);
-                if (red) nacc += site_norm2<R>(acc[k]);
+                if (red && slot >= 0) nacc += site_norm2<R>(acc[k]);
+                if (MODE == 3) {
+                    // x += alpha p at this (j, s); x and p belong to the other checkerboard,
+                    // the update is elementwise
+                    cpx<R> pv[12];
+                    cpx<RX> xv[12];
+                    Field<P>::load_stream(ep.aux, j, sv[k], Ls, n5, pv);
+                    Field<PX>::load_stream(ep.out2, j, sv[k], Ls, n5, xv);
+#pragma unroll
+                    for (int c = 0; c < 12; c++)
+                        xv[c] = mk((RX)(xv[c].re + ax * (RX)pv[c].re), (RX)(xv[c].im + ax * (RX)pv[c].im));
+                    Field<PX>::store_stream(ep.out2, j, sv[k], Ls, n5, xv);
+                    // r -= alpha q
+                    cpx<R> qv[12], rv[12];
+                    Field<P>::load_stream(ep.aux2, j, sv[k], Ls, n5, qv);
+                    Field<P>::load_stream(ep.out3, j, sv[k], Ls, n5, rv);
+#pragma unroll
+                    for (int c = 0; c < 12; c++) rv[c] = rv[c] - (R)ax * qv[c];
+                    Field<P>::store_stream(ep.out3, j, sv[k], Ls, n5, rv);
+                    nacc2 += site_norm2<R>(rv);
+                }
             }
         }
         if (MODE == 1) {
@@ -710,8 +742,10 @@ __global__ void __launch_bounds__(256, SPT == 2 ? 2 : (MODE == 1 ? EOFA_MODE1_MI
         }
         if (HASOP) __syncthreads();
     }
-    if (red) {
-        if (MODE == 2) grid_sum2(nacc, nacc2, red, slot, ep.slot2);
+    if (MODE == 3) {
+        grid_sum(nacc2, red, ep.slot2);
+    } else if (red && slot >= 0) {
+        if (MODE == 2 && ep.out2 != nullptr) grid_sum2(nacc, nacc2, red, slot, ep.slot2);
         else grid_sum(nacc, red, slot);
     }
 }
@@ -787,7 +821,7 @@ __global__ void __launch_bounds__(256, 3) local5_kernel(Geom g, Op5 op, const vo
     if (red) grid_sum(nacc, red, slot);
 }
 
-// x += alpha p (x in PX), p = s + beta p
+// x += alpha p (x in PX; skipped when x is null), p = s + beta p
 template <int P, int PX>
 __global__ void __launch_bounds__(256) xp_update_kernel(Geom g, const double* sc, int it, void* x, void* p,
                                                         const void* s) {
@@ -800,16 +834,18 @@ __global__ void __launch_bounds__(256) xp_update_kernel(Geom g, const double* sc
         const int j = (int)(t / Lsu);
         const int ss = (int)(t - (unsigned)j * Lsu);
         cpx<R> pv[12], sv[12];
-        cpx<RX> xv[12];
         Field<P>::load(p, j, ss, g.Ls, n5, pv);
         Field<P>::load(s, j, ss, g.Ls, n5, sv);
-        Field<PX>::load(x, j, ss, g.Ls, n5, xv);
+        if (x != nullptr) {
+            cpx<RX> xv[12];
+            Field<PX>::load(x, j, ss, g.Ls, n5, xv);
 #pragma unroll
-        for (int k = 0; k < 12; k++) {
-            xv[k] = mk((RX)(xv[k].re + (RX)alpha * (RX)pv[k].re), (RX)(xv[k].im + (RX)alpha * (RX)pv[k].im));
-            pv[k] = sv[k] + beta * pv[k];
+            for (int k = 0; k < 12; k++)
+                xv[k] = mk((RX)(xv[k].re + (RX)alpha * (RX)pv[k].re), (RX)(xv[k].im + (RX)alpha * (RX)pv[k].im));
+            Field<PX>::store(x, j, ss, g.Ls, n5, xv);
         }
-        Field<PX>::store(x, j, ss, g.Ls, n5, xv);
+#pragma unroll
+        for (int k = 0; k < 12; k++) pv[k] = sv[k] + beta * pv[k];
         Field<P>::store(p, j, ss, g.Ls, n5, pv);
     }
 }
@@ -867,6 +903,9 @@ void launch_with(K k, const eofa_ctx* ctx, const Geom& g, int NS, int spt, size_
     Epi ep;
     ep.op2 = op;
     ep.out2 = nullptr;
+    ep.aux = nullptr;
+    ep.out3 = nullptr;
+    ep.aux2 = nullptr;
     ep.it = 0;
     ep.slot2 = 0;
     k<<<grid, threads, smem, st>>>(g, par, in, out, gauge, op, y, a_out, b_in, red, slot, NS, ep);
@@ -1083,7 +1122,7 @@ void launch_dslash_epi_t(const eofa_ctx* ctx, int par, const void* in, void* out
     typedef typename Field<P>::R R;
     Geom g = ctx_geom(ctx);
     const void* gauge = ctx->gauge[P == P64 ? P64 : P32];
-    constexpr bool HASOP = MODE == 1;
+    constexpr bool HASOP = MODE == 1 || MODE == 3;
     const long long key = ((((long long)P * 2 + DAG) * 128 + g.Ls) * 2 + (HASOP ? 1 : 0)) * 2 + (y ? 1 : 0);
     int NS = pick_ns(g.Ls, sizeof(cpx<R>));
     auto it = ctx->tuned->find(key);
@@ -1184,7 +1223,10 @@ void xp_update_prec(const eofa_ctx* ctx, const double* sc, int it, void* x, void
                           void* out2, cudaStream_t st);                                                         \
     void dslash_z_##NAME(const eofa_ctx* ctx, int par, int dag, const void* in, void* z, const Op5& op,         \
                          const void* y, double a_out, double b_in, double* red, int slot, int it, void* r,      \
-                         int rslot, cudaStream_t st);
+                         int rslot, cudaStream_t st);                                                           \
+    void dslash_x_##NAME(const eofa_ctx* ctx, int par, int dag, const void* in, void* out, const Op5& op,       \
+                         double* red, int it, void* x, const void* p, void* r, const void* q, int rslot,        \
+                         cudaStream_t st);
 DSL_DECLARE(p64)
 DSL_DECLARE(p32)
 DSL_DECLARE(p16)
@@ -1209,6 +1251,9 @@ DSL_DECLARE(p16)
         dsl::Epi ep;                                                                                            \
         ep.op2 = op2;                                                                                           \
         ep.out2 = out2;                                                                                         \
+        ep.aux = nullptr;                                                                                       \
+        ep.out3 = nullptr;                                                                                      \
+        ep.aux2 = nullptr;                                                                                      \
         ep.it = 0;                                                                                              \
         ep.slot2 = 0;                                                                                           \
         dsl::dslash_epi_prec<P, 1>(ctx, par, dag, in, out, op, y, a_out, b_in, red, slot, ep, st);              \
@@ -1219,7 +1264,23 @@ DSL_DECLARE(p16)
         dsl::Epi ep;                                                                                            \
         ep.op2 = op;                                                                                            \
         ep.out2 = r;                                                                                            \
+        ep.aux = nullptr;                                                                                       \
+        ep.out3 = nullptr;                                                                                      \
+        ep.aux2 = nullptr;                                                                                      \
         ep.it = it;                                                                                             \
         ep.slot2 = rslot;                                                                                       \
         dsl::dslash_epi_prec<P, 2>(ctx, par, dag, in, z, op, y, a_out, b_in, red, slot, ep, st);                \
+    }                                                                                                           \
+    void dslash_x_##NAME(const eofa_ctx* ctx, int par, int dag, const void* in, void* out, const Op5& op,       \
+                         double* red, int it, void* x, const void* p, void* r, const void* q, int rslot,        \
+                         cudaStream_t st) {                                                                     \
+        dsl::Epi ep;                                                                                            \
+        ep.op2 = op;                                                                                            \
+        ep.out2 = x;                                                                                            \
+        ep.aux = p;                                                                                             \
+        ep.out3 = r;                                                                                            \
+        ep.aux2 = q;                                                                                            \
+        ep.it = it;                                                                                             \
+        ep.slot2 = rslot;                                                                                       \
+        dsl::dslash_epi_prec<P, 3>(ctx, par, dag, in, out, op, nullptr, 1.0, 0.0, red, -1, ep, st);             \
     }

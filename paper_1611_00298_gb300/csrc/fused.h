@@ -29,18 +29,25 @@ void fused_dslash(const eofa_ctx* ctx, int prec, int out_parity, int dagger, con
 //   fused_dslash_to: out = a_out (-1/2) B[hop(in)] + b_in y, |out|^2 -> red[slot],
 //                    out2 = B2 out (a second 5D-local block applied in the epilogue)
 //   fused_dslash_z:  with alpha = alpha(red, it) and w = a_out (-1/2) B[hop(in)] + b_in y:
-//                    z <- z - alpha w, |z|^2 -> red[slot];  r <- r - alpha y, |r|^2 -> red[rslot]
+//                    z <- z - alpha w, |z|^2 -> red[slot];  when r is not null also
+//                    r <- r - alpha y, |r|^2 -> red[rslot]
 void fused_dslash_to(const eofa_ctx* ctx, int prec, int out_parity, int dagger, const void* in, void* out,
                      const Op5& op, const void* y, double a_out, double b_in, double* red, int slot, const Op5& op2,
                      void* out2, cudaStream_t st);
 void fused_dslash_z(const eofa_ctx* ctx, int prec, int out_parity, int dagger, const void* in, void* z, const Op5& op,
                     const void* y, double a_out, double b_in, double* red, int slot, int it, void* r, int rslot,
                     cudaStream_t st);
+//   fused_dslash_x:  out = (-1/2) B[hop(in)], and x <- x + alpha(red, it) p, r <- r - alpha q
+//                    elementwise at the same (j, s), |r|^2 -> red[rslot] (x in the solution
+//                    precision: FP32 for FP16 fields)
+void fused_dslash_x(const eofa_ctx* ctx, int prec, int out_parity, int dagger, const void* in, void* out,
+                    const Op5& op, double* red, int it, void* x, const void* p, void* r, const void* q, int rslot,
+                    cudaStream_t st);
 // x' = x + c z (c = -alpha(sc, it) if use_alpha else c0); xw <- x'; |x'|^2 -> red[slot]; out = a_out B x'
 void fused_local5(const eofa_ctx* ctx, int prec, const Op5& op, const void* x, const void* z, double c0,
                   const double* sc, int it, int use_alpha, void* xw, void* out, double a_out, double* red, int slot,
                   cudaStream_t st);
-// x += alpha p ; p = s + beta p   (alpha, beta from sc at iteration it)
+// x += alpha p (skipped when x is null); p = s + beta p   (alpha, beta from sc at iteration it)
 void fused_xp_update(const eofa_ctx* ctx, int prec, int precx, const double* sc, int it, void* x, void* p,
                      const void* s, cudaStream_t st);
 Op5 op_identity();

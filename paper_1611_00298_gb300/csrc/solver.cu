@@ -13,9 +13,10 @@
 // tracking r = f^ - A x and the normal residual s = A^+ r) iterates in the
 // inner precision with five fused launches per iteration (enqueue):
 //   te = G'^-1 D_eo p;  q = p - G'^-1 D_oe te, |q|^2 = delta, to = G'^-T q;
-//   te = G'^-T D^+_eo to;
-//   s <- s - alpha (q - D^+_oe te) = s - alpha A^+ q,  r <- r - alpha q,
-//   gamma' = |s|^2, |r|^2;  x += alpha p, p = s + beta p.
+//   te = G'^-T D^+_eo to, with x += alpha p and r <- r - alpha q, |r|^2
+//   elementwise in the same launch;
+//   s <- s - alpha (q - D^+_oe te) = s - alpha A^+ q, gamma' = |s|^2;
+//   p = s + beta p.
 // With mixed precision the residual is recomputed in FP64 whenever |r| has
 // dropped by the factor delta since the last recomputation (reliable
 // updates; they also reset s = A^+ r), and the solution accumulates in
@@ -88,7 +89,7 @@ void Solve::setup(eofa_ctx* c, const eofa_solve_params& prm, const double* b_dev
     precx = mixed ? P32 : P64;
     // reliable-update threshold: delta <= 0 picks the default of the inner
     // precision; FP16 storage cannot follow the residual down more than ~1e-2
-    const double auto_delta = prec == P16 ? 0.1 : 1e-3;
+    const double auto_delta = prec == P16 ? 0.1 : 1e-4;
     delta = (P.delta > 0 && P.delta < 1) ? P.delta : auto_delta;
     if (prec == P16 && delta < 0.05) delta = 0.05;
     S = P.system == EOFA_SYS_DWF ? system_dwf(P.alpha, P.M5, P.mf)
@@ -221,12 +222,14 @@ void Solve::enqueue(int n, cudaStream_t st) {
         // q = A p, |q|^2 -> delta, to = G'^-T q
         fused_dslash(ctx, prec, 0, 0, p, te, Gi, nullptr, 1.0, 0.0, nullptr, 0, st);
         fused_dslash_to(ctx, prec, 1, 0, te, q, Gi, p, -1.0, 1.0, red, SC_DELTA, GiT, to, st);
-        // s -= alpha A^+ q, |s|^2 -> gamma (next parity); r -= alpha q, |r|^2 -> ring
-        fused_dslash(ctx, prec, 0, 1, to, te, GiT, nullptr, 1.0, 0.0, nullptr, 0, st);
-        fused_dslash_z(ctx, prec, 1, 1, te, s, op_identity(), q, -1.0, 1.0, red, SC_GAMMA + ((it + 1) & 1), it, r,
-                       SC_RRH + (it % ring), st);
-        // x += alpha p; p = s + beta p
-        fused_xp_update(ctx, prec, precx, red, it, x, p, s, st);
+        // te = G'^-T D^+_eo to, with x += alpha p and r -= alpha q, |r|^2 -> ring riding along
+        // (alpha is known once delta is)
+        fused_dslash_x(ctx, prec, 0, 1, to, te, GiT, red, it, x, p, r, q, SC_RRH + (it % ring), st);
+        // s -= alpha A^+ q, |s|^2 -> gamma (next parity)
+        fused_dslash_z(ctx, prec, 1, 1, te, s, op_identity(), q, -1.0, 1.0, red, SC_GAMMA + ((it + 1) & 1), it,
+                       nullptr, 0, st);
+        // p = s + beta p
+        fused_xp_update(ctx, prec, precx, red, it, nullptr, p, s, st);
     }
     inf.iters += n;
 }
