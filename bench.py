@@ -501,6 +501,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="f32", choices=["f32", "f16"])
+    ap.add_argument("--cg-form", default="auto", choices=["auto", "five", "six"],
+                    help="CG iteration form (auto: timed on the first solve)")
     ap.add_argument("--small", action="store_true", help="8^4 x 8 lattice (quick check)")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 solve comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
@@ -570,6 +572,8 @@ def main():
     phi_np = inputs.fermion4d(wl["dims"], replica_seed(wl["seed"], rank))
     lat = eofa.Lattice(wl["dims"], Ls, bc_t=wl["bc"])
     lat.gauge_load(U)
+    if args.cg_form != "auto":
+        lat.set_cg_form(prec, eofa.CG_FORM_FIVE if args.cg_form == "five" else eofa.CG_FORM_SIX)
     phi = torch.from_numpy(phi_np).cuda()
     F = torch.empty(lat.shapeU, dtype=torch.complex128, device="cuda")
     kw = dict(alpha=wl["alpha"], M5=wl["M5"], m1=wl["m1"], m2=wl["m2"], precision=prec, tol=1e-10)
@@ -680,7 +684,9 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
             "data": "synthetic (seeded SU(3) links and Gaussian pseudofermion; no ensemble)",
             "config": workload_config(wl),
-            "solver": f"mixed {args.precision.upper()} inner CG, FP64 reliable updates",
+            "solver": f"mixed {args.precision.upper()} inner CG, FP64 reliable updates, "
+                      f"{ {0: 'five', 1: 'six'}.get(lat.cg_form(prec), 'undecided') }-launch iteration "
+                      f"({'timed' if args.cg_form == 'auto' else 'forced'})",
             "roofline": roofline, "e2e": e2e, "solve": solve, "clocks": clk, "gpu_launches": int(launches),
             "hop_launches_by_precision": {"fp64": hop_launches[0], "fp32": hop_launches[1], "fp16": hop_launches[2]},
             "action": actions[-1],

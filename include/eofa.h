@@ -211,6 +211,28 @@ int eofa_pseudofermion_solutions_dev(eofa_ctx* ctx, int Ls, double alpha, double
  * precision's default as in eofa_solve_params). */
 int eofa_set_reliable_delta(eofa_ctx* ctx, double delta);
 
+/* CG iteration form of the solves on this context at one precision
+ * (EOFA_PREC_*; the form applies to the inner iterations).  Both forms are
+ * the same CG on the normal equations of Sec. 5.1 and give the same
+ * iterates up to rounding:
+ *   EOFA_CG_FORM_FIVE: five fused launches per iteration; the normal
+ *     residual s = A^+ r is carried by the update s -= alpha A^+ q;
+ *   EOFA_CG_FORM_SIX: six fused launches that stream fewer bytes; s is
+ *     formed from r every iteration.
+ * EOFA_CG_FORM_AUTO (the default) times both forms, on real iterations of
+ * the first solve that runs a chunk of at least six iterations outside
+ * stream capture, and keeps the faster for the context's lifetime; until
+ * then the five-launch form runs below 2^22 five-dimensional sites per
+ * checkerboard and the six-launch form above.  Setting AUTO again forgets
+ * the timed choice.  eofa_get_cg_form writes the form in use, or
+ * EOFA_CG_FORM_AUTO while it is undecided.  EOFA_EINVAL for a bad
+ * precision or form. */
+#define EOFA_CG_FORM_AUTO (-1)
+#define EOFA_CG_FORM_FIVE 0
+#define EOFA_CG_FORM_SIX 1
+int eofa_set_cg_form(eofa_ctx* ctx, int precision, int form);
+int eofa_get_cg_form(const eofa_ctx* ctx, int precision, int* form);
+
 /* Leapfrog molecular-dynamics trajectory for H = sum_links tr P^2 + S_EOFA
  * (Eq. (5), force Eq. (7)): P <- P - dtau/2 F, then nsteps times
  * {U <- exp(i dtau P) U; P <- P - dtau F} with the last momentum step halved.
@@ -326,6 +348,30 @@ typedef struct {
 int eofa_hmc_dev(eofa_ctx* ctx, const eofa_md_params* md, int ntraj, double alpha0, int npoles,
                  const double* alphas, const double* betas, const double* P_dev, const double* eta_dev,
                  const double* u, double* U_dev, eofa_hmc_traj_info* info, void* stream);
+
+/* Checkpoint / resume (Sec. 5 production runs restart from saved
+ * configurations).  A checkpoint file holds one field in the host
+ * canonical layout, the gauge field U or the momenta P (both 4 V 3x3
+ * complex = 72 V doubles), after a 64-byte little-endian header: magic
+ * "EOFACKPT", version 1, kind, dims {X, Y, Z, T}, the number of doubles,
+ * the caller's trajectory number and the FNV-1a 64-bit checksum of the
+ * data bytes.  Host-only, no GPU needed.
+ *   eofa_checkpoint_write: data (host, 72 V doubles) -> path; EOFA_EINVAL for
+ *     bad arguments or an unwritable path, EOFA_EDEVICE for a short write.
+ *   eofa_checkpoint_read: path -> data (host, caller-owned, 72 V doubles) and
+ *     traj (may be NULL); EOFA_EINVAL when the file is missing, of another
+ *     kind or lattice, truncated, longer than its header says or fails the
+ *     checksum (data is then left unchanged).
+ * eofa_gauge_save writes the context's current links (after an HMC chain,
+ * the chain's state); eofa_gauge_restore reads a gauge checkpoint of the
+ * context's lattice and loads it as eofa_gauge_load does (unitarity
+ * check included). */
+#define EOFA_CKPT_GAUGE 0
+#define EOFA_CKPT_MOMENTA 1
+int eofa_checkpoint_write(const char* path, int kind, const int dims[4], long long traj, const double* data);
+int eofa_checkpoint_read(const char* path, int kind, const int dims[4], long long* traj, double* data);
+int eofa_gauge_save(eofa_ctx* ctx, const char* path, long long traj);
+int eofa_gauge_restore(eofa_ctx* ctx, const char* path, long long* traj);
 
 /* Molecular dynamics link update U <- exp(i eps P) U on the device gauge
  * field of the context and on the canonical copy U_dev (if not NULL);

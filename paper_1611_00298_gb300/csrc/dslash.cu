@@ -84,9 +84,10 @@ void fused_dslash_x(const eofa_ctx* ctx, int prec, int out_parity, int dagger, c
                     cudaStream_t st) {
     const Op5 opf = op_finalize(op, ctx->Ls);
     const double n5h = (double)ctx->Vh * ctx->Ls;
-    // in, out; p, q read; x and r read and written (x in FP32 when the field is FP16)
+    // in, out, p read, x read and written; with r: q read, r read and written (x in FP32 when the field is FP16)
     const double xb = prec == P16 ? 96.0 : spinor_bytes(prec);
-    const double bytes = n5h * (spinor_bytes(prec) * 6.0 + 2.0 * xb) + 8.0 * ctx->Vh * (prec == P64 ? 144.0 : 72.0);
+    const double bytes = n5h * (spinor_bytes(prec) * (r ? 6.0 : 3.0) + 2.0 * xb) +
+                         8.0 * ctx->Vh * (prec == P64 ? 144.0 : 72.0);
     prof_begin(ctx, prec, st, bytes);
     if (prec == P64) dslash_x_p64(ctx, out_parity, dagger, in, out, opf, red, it, x, p, r, q, rslot, st);
     else if (prec == P32) dslash_x_p32(ctx, out_parity, dagger, in, out, opf, red, it, x, p, r, q, rslot, st);

@@ -590,9 +590,10 @@ struct Epi {
 // out <- out - alpha(red, it) value, and so is out2 <- out2 - alpha y, with
 // |out|^2 -> red[slot] and |out2|^2 -> red[ep.slot2] (out2 may be null).
 // MODE 3: out = value, and the CG updates x <- x + alpha(red, it) p and
-// r <- r - alpha q at the same (j, s), |r|^2 -> red[ep.slot2] (x = out2 in
-// the solution's precision, p = aux, r = out3, q = aux2): elementwise
-// updates ride in this latency-bound launch instead of streaming kernels.
+// (when r = out3 is not null) r <- r - alpha q at the same (j, s),
+// |r|^2 -> red[ep.slot2] (x = out2 in the solution's precision, p = aux,
+// q = aux2): elementwise updates ride in this latency-bound launch instead
+// of streaming kernels.
 // SPT slices per thread: thread (site, sh) handles s = sh + k Ls/SPT,
 // k < SPT, so neighbour indices and link rows are loaded once for SPT output
 // sites (Ls/SPT threads per site; SPT = 2 needs an even Ls).
@@ -712,14 +713,16 @@ __global__ void __launch_bounds__(256, SPT == 2 ? 2 : (MODE == 1 ? EOFA_MODE1_MI
                     for (int c = 0; c < 12; c++)
                         xv[c] = mk((RX)(xv[c].re + ax * (RX)pv[c].re), (RX)(xv[c].im + ax * (RX)pv[c].im));
                     Field<PX>::store_stream(ep.out2, j, sv[k], Ls, n5, xv);
-                    // r -= alpha q
-                    cpx<R> qv[12], rv[12];
-                    Field<P>::load_stream(ep.aux2, j, sv[k], Ls, n5, qv);
-                    Field<P>::load_stream(ep.out3, j, sv[k], Ls, n5, rv);
+                    if (ep.out3 != nullptr) {
+                        // r -= alpha q
+                        cpx<R> qv[12], rv[12];
+                        Field<P>::load_stream(ep.aux2, j, sv[k], Ls, n5, qv);
+                        Field<P>::load_stream(ep.out3, j, sv[k], Ls, n5, rv);
 #pragma unroll
-                    for (int c = 0; c < 12; c++) rv[c] = rv[c] - (R)ax * qv[c];
-                    Field<P>::store_stream(ep.out3, j, sv[k], Ls, n5, rv);
-                    nacc2 += site_norm2<R>(rv);
+                        for (int c = 0; c < 12; c++) rv[c] = rv[c] - (R)ax * qv[c];
+                        Field<P>::store_stream(ep.out3, j, sv[k], Ls, n5, rv);
+                        nacc2 += site_norm2<R>(rv);
+                    }
                 }
             }
         }
@@ -743,7 +746,7 @@ __global__ void __launch_bounds__(256, SPT == 2 ? 2 : (MODE == 1 ? EOFA_MODE1_MI
         if (HASOP) __syncthreads();
     }
     if (MODE == 3) {
-        grid_sum(nacc2, red, ep.slot2);
+        if (ep.out3 != nullptr) grid_sum(nacc2, red, ep.slot2);
     } else if (red && slot >= 0) {
         if (MODE == 2 && ep.out2 != nullptr) grid_sum2(nacc, nacc2, red, slot, ep.slot2);
         else grid_sum(nacc, red, slot);

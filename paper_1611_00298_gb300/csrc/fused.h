@@ -37,9 +37,9 @@ void fused_dslash_to(const eofa_ctx* ctx, int prec, int out_parity, int dagger, 
 void fused_dslash_z(const eofa_ctx* ctx, int prec, int out_parity, int dagger, const void* in, void* z, const Op5& op,
                     const void* y, double a_out, double b_in, double* red, int slot, int it, void* r, int rslot,
                     cudaStream_t st);
-//   fused_dslash_x:  out = (-1/2) B[hop(in)], and x <- x + alpha(red, it) p, r <- r - alpha q
-//                    elementwise at the same (j, s), |r|^2 -> red[rslot] (x in the solution
-//                    precision: FP32 for FP16 fields)
+//   fused_dslash_x:  out = (-1/2) B[hop(in)], and x <- x + alpha(red, it) p and (r not null)
+//                    r <- r - alpha q elementwise at the same (j, s), |r|^2 -> red[rslot] (x in
+//                    the solution precision: FP32 for FP16 fields)
 void fused_dslash_x(const eofa_ctx* ctx, int prec, int out_parity, int dagger, const void* in, void* out,
                     const Op5& op, double* red, int it, void* x, const void* p, void* r, const void* q, int rslot,
                     cudaStream_t st);

@@ -11,12 +11,20 @@
 //   A^+ = 1 - D^dag_oe G'^{-T} D^dag_eo G'^{-T}  (D^dag: hop with swapped projectors).
 // CG on the normal equations A^+ A x = A^+ f^ (the least-squares form,
 // tracking r = f^ - A x and the normal residual s = A^+ r) iterates in the
-// inner precision with five fused launches per iteration (enqueue):
+// inner precision in one of two forms of fused launches (iterate):
+// five launches,
 //   te = G'^-1 D_eo p;  q = p - G'^-1 D_oe te, |q|^2 = delta, to = G'^-T q;
 //   te = G'^-T D^+_eo to, with x += alpha p and r <- r - alpha q, |r|^2
 //   elementwise in the same launch;
 //   s <- s - alpha (q - D^+_oe te) = s - alpha A^+ q, gamma' = |s|^2;
+//   p = s + beta p,
+// or six launches that move fewer bytes (s is formed from r, not updated),
+//   te = G'^-1 D_eo p;  q = p - G'^-1 D_oe te, |q|^2 = delta;
+//   r <- r - alpha q, |r|^2, to = G'^-T r;
+//   te = G'^-T D^+_eo to, with x += alpha p in the same launch;
+//   s = r - D^+_oe te = A^+ r, gamma' = |s|^2;
 //   p = s + beta p.
+// Which one runs is timed per context (Solve::enqueue).
 // With mixed precision the residual is recomputed in FP64 whenever |r| has
 // dropped by the factor delta since the last recomputation (reliable
 // updates; they also reset s = A^+ r), and the solution accumulates in
@@ -191,34 +199,26 @@ bool Solve::start_cg(cudaStream_t st) {
     return true;
 }
 
-// EOFA_CG=cgls selects the six-launch CG of the least-squares form, which
-// updates r itself (r -= alpha q) and forms s = A^+ r from it every
-// iteration, instead of the five-launch iteration on the normal residual.
-static bool use_cgls() {
-    static const int v = [] {
-        const char* e = getenv("EOFA_CG");
-        return (e && std::string(e) == "cgls") ? 1 : 0;
-    }();
-    return v != 0;
-}
-
 static bool solve_log() {
     static const int v = getenv("EOFA_SOLVE_LOG") ? 1 : 0;
     return v != 0;
 }
 
-void Solve::enqueue(int n, cudaStream_t st) {
-    if (use_cgls()) {
-        for (int k = 0; k < n; k++, it++) {
-            apply_A(ctx, Gi, prec, p, q, te, red, SC_DELTA, st);
-            apply_Adag_cg(ctx, GiT, prec, r, q, red, it, s, te, to, SC_RRH + (it % ring), SC_GAMMA + ((it + 1) & 1),
-                          st);
-            fused_xp_update(ctx, prec, precx, red, it, x, p, s, st);
-        }
-        inf.iters += n;
-        return;
-    }
-    for (int k = 0; k < n; k++, it++) {
+// One CG iteration in the given form.  Both forms leave the same state at
+// the iteration boundary (x, r, p, s = A^+ r, |r|^2 in the ring slot of the
+// iteration, gamma in the slot of the next parity), so a solve may switch
+// between them at any iteration.
+void Solve::iterate(int form, cudaStream_t st) {
+    if (form == EOFA_CG_FORM_SIX) {
+        // q = A p, |q|^2 -> delta
+        apply_A(ctx, Gi, prec, p, q, te, red, SC_DELTA, st);
+        // r -= alpha q, |r|^2 -> ring, to = G'^-T r
+        fused_local5(ctx, prec, GiT, r, q, 0.0, red, it, 1, r, to, 1.0, red, SC_RRH + (it % ring), st);
+        // te = G'^-T D^+_eo to, with x += alpha p riding along
+        fused_dslash_x(ctx, prec, 0, 1, to, te, GiT, red, it, x, p, nullptr, nullptr, 0, st);
+        // s = r - D^+_oe te = A^+ r, |s|^2 -> gamma (next parity)
+        fused_dslash(ctx, prec, 1, 1, te, s, op_identity(), r, -1.0, 1.0, red, SC_GAMMA + ((it + 1) & 1), st);
+    } else {
         // q = A p, |q|^2 -> delta, to = G'^-T q
         fused_dslash(ctx, prec, 0, 0, p, te, Gi, nullptr, 1.0, 0.0, nullptr, 0, st);
         fused_dslash_to(ctx, prec, 1, 0, te, q, Gi, p, -1.0, 1.0, red, SC_DELTA, GiT, to, st);
@@ -228,9 +228,69 @@ void Solve::enqueue(int n, cudaStream_t st) {
         // s -= alpha A^+ q, |s|^2 -> gamma (next parity)
         fused_dslash_z(ctx, prec, 1, 1, te, s, op_identity(), q, -1.0, 1.0, red, SC_GAMMA + ((it + 1) & 1), it,
                        nullptr, 0, st);
-        // p = s + beta p
-        fused_xp_update(ctx, prec, precx, red, it, nullptr, p, s, st);
     }
+    // p = s + beta p
+    fused_xp_update(ctx, prec, precx, red, it, nullptr, p, s, st);
+    it++;
+}
+
+// The iteration form of a context and inner precision: set by
+// eofa_set_cg_form, else timed on the first chunk of at least
+// FORM_TUNE_MIN iterations that runs outside stream capture.  The timing
+// runs real CG iterations: one warm-up iteration per form (it lets the
+// kernel autotuner settle), then blocks of m iterations in the order
+// five, six, six, five with CUDA events on the solve's stream; the form
+// with the smaller total wins.  Until then (short chunks, capture), the
+// five-launch form runs below FORM_SIX_SITES sites per checkerboard and
+// the six-launch form above, where bytes rather than launches set the
+// iteration time.
+static constexpr int FORM_TUNE_MIN = 6;
+static constexpr long long FORM_SIX_SITES = 1LL << 22;
+
+static long long form_key(int prec) { return -1 - (long long)prec; }
+
+int Solve::tune_form(int n, cudaStream_t st) {
+    iterate(EOFA_CG_FORM_FIVE, st);
+    iterate(EOFA_CG_FORM_SIX, st);
+    const int m = (n - 2) / 4;
+    const int order[4] = {EOFA_CG_FORM_FIVE, EOFA_CG_FORM_SIX, EOFA_CG_FORM_SIX, EOFA_CG_FORM_FIVE};
+    cudaEvent_t ev[5];
+    for (auto& e : ev) EOFA_CUDA(cudaEventCreate(&e));
+    EOFA_CUDA(cudaEventRecord(ev[0], st));
+    for (int b = 0; b < 4; b++) {
+        for (int k = 0; k < m; k++) iterate(order[b], st);
+        EOFA_CUDA(cudaEventRecord(ev[b + 1], st));
+    }
+    EOFA_CUDA(cudaEventSynchronize(ev[4]));
+    float ms[4];
+    for (int b = 0; b < 4; b++) EOFA_CUDA(cudaEventElapsedTime(&ms[b], ev[b], ev[b + 1]));
+    for (auto& e : ev) EOFA_CUDA(cudaEventDestroy(e));
+    const int form = ms[0] + ms[3] <= ms[1] + ms[2] ? EOFA_CG_FORM_FIVE : EOFA_CG_FORM_SIX;
+    (*ctx->tuned)[form_key(prec)] = form;
+    if (getenv("EOFA_TUNE_LOG"))
+        fprintf(stderr, "cg form (precision %d, %d iterations each): five %.4f ms, six %.4f ms per iteration -> %s\n",
+                prec, 2 * m, (ms[0] + ms[3]) / (2 * m), (ms[1] + ms[2]) / (2 * m),
+                form == EOFA_CG_FORM_FIVE ? "five" : "six");
+    return 2 + 4 * m;
+}
+
+void Solve::enqueue(int n, cudaStream_t st) {
+    int done_here = 0;
+    int form;
+    auto f = ctx->tuned->find(form_key(prec));
+    if (f != ctx->tuned->end()) {
+        form = f->second;
+    } else {
+        cudaStreamCaptureStatus cs;
+        EOFA_CUDA(cudaStreamIsCapturing(st, &cs));
+        if (cs == cudaStreamCaptureStatusNone && n >= FORM_TUNE_MIN) {
+            done_here = tune_form(n, st);
+            form = ctx->tuned->at(form_key(prec));
+        } else {
+            form = (long long)ctx->Vh * ctx->Ls >= FORM_SIX_SITES ? EOFA_CG_FORM_SIX : EOFA_CG_FORM_FIVE;
+        }
+    }
+    for (int k = done_here; k < n; k++) iterate(form, st);
     inf.iters += n;
 }
 
@@ -371,6 +431,23 @@ int solve_dev_impl(eofa_ctx* ctx, const eofa_solve_params* prm, const double* b_
 }
 
 extern "C" {
+
+int eofa_set_cg_form(eofa_ctx* ctx, int precision, int form) {
+    if (!ctx) return EOFA_EINVAL;
+    if (precision < EOFA_PREC_F64 || precision > EOFA_PREC_MIXED_F16)
+        return fail(ctx, EOFA_EINVAL, "precision must be an EOFA_PREC_* value");
+    if (form == EOFA_CG_FORM_AUTO) ctx->tuned->erase(form_key(precision));
+    else if (form == EOFA_CG_FORM_FIVE || form == EOFA_CG_FORM_SIX) (*ctx->tuned)[form_key(precision)] = form;
+    else return fail(ctx, EOFA_EINVAL, "form must be EOFA_CG_FORM_AUTO, _FIVE or _SIX");
+    return EOFA_OK;
+}
+
+int eofa_get_cg_form(const eofa_ctx* ctx, int precision, int* form) {
+    if (!ctx || !form || precision < EOFA_PREC_F64 || precision > EOFA_PREC_MIXED_F16) return EOFA_EINVAL;
+    auto f = ctx->tuned->find(form_key(precision));
+    *form = f != ctx->tuned->end() ? f->second : EOFA_CG_FORM_AUTO;
+    return EOFA_OK;
+}
 
 int eofa_solve_dev(eofa_ctx* ctx, const eofa_solve_params* p, const double* b_dev, double* x_dev, eofa_solve_info* info,
                    void* stream) {

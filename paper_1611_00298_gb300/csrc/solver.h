@@ -3,7 +3,7 @@
 #include "api_util.h"
 #include "fused.h"
 
-// One even-odd CGLS solve of (D_hop + G') psi = f (see solver.cu).  The
+// One even-odd CG solve of (D_hop + G') psi = f (see solver.cu).  The
 // iteration kernels read and write only this object's reduction scratch
 // `red`, so several solves can run concurrently on one context.
 struct Solve {
@@ -31,8 +31,13 @@ struct Solve {
                double* red_scratch, int ring_len, cudaStream_t st);
     // start a CG run from the current FP64 iterate x_o; returns false if already converged
     bool start_cg(cudaStream_t st);
-    // queue n CG iterations (no host synchronisation)
+    // queue n CG iterations (no host synchronisation, except once per context and
+    // precision when the iteration form is timed)
     void enqueue(int n, cudaStream_t st);
+    // one CG iteration in form EOFA_CG_FORM_FIVE or EOFA_CG_FORM_SIX
+    void iterate(int form, cudaStream_t st);
+    // time both forms on real iterations of this solve; returns the iterations run
+    int tune_form(int n, cudaStream_t st);
     // after a queued chunk: read |r|^2, do a reliable update if due; sets done when the inner target is met
     void check(int n, cudaStream_t st);
     // the same with |r|^2 already read back by the caller

@@ -33,8 +33,11 @@ EXPORTS = [
     "eofa_dwf_apply_noalloc", "eofa_schur_hop_dev", "eofa_pseudofermion_solutions_dev",
     "eofa_set_reliable_delta", "eofa_leapfrog_dev", "eofa_rational_inv_sqrt", "eofa_heatbath_dev",
     "eofa_gauge_action_dev", "eofa_gauge_force_dev", "eofa_hmc_trajectory_dev", "eofa_force_parts_dev",
-    "eofa_check_device", "eofa_hmc_dev", "eofa_probe_fp64_fma",
+    "eofa_check_device", "eofa_hmc_dev", "eofa_probe_fp64_fma", "eofa_checkpoint_write", "eofa_checkpoint_read",
+    "eofa_gauge_save", "eofa_gauge_restore", "eofa_set_cg_form", "eofa_get_cg_form",
 ]
+CKPT_GAUGE, CKPT_MOMENTA = 0, 1
+CG_FORM_AUTO, CG_FORM_FIVE, CG_FORM_SIX = -1, 0, 1
 INT_LEAPFROG, INT_FG_PQPQP, INT_FG_QPQPQ = 0, 1, 2
 
 
@@ -135,6 +138,8 @@ def load_library(path: str = LIB_PATH):
         "eofa_pseudofermion_solutions_dev": (I, [P, I, D, D, D, D, I, D, P, P, P, ctypes.POINTER(D),
                                                  ctypes.POINTER(SolveInfo), P]),
         "eofa_set_reliable_delta": (I, [P, D]),
+        "eofa_set_cg_form": (I, [P, I, I]),
+        "eofa_get_cg_form": (I, [P, I, ctypes.POINTER(I)]),
         "eofa_gauge_action_dev": (I, [P, D, P, ctypes.POINTER(D), P]),
         "eofa_check_device": (I, [P, P]),
         "eofa_force_parts_dev": (I, [P, I, D, D, D, D, I, D, P, P, P, ctypes.POINTER(SolveInfo), P]),
@@ -145,6 +150,10 @@ def load_library(path: str = LIB_PATH):
         "eofa_leapfrog_dev": (I, [P, I, D, D, D, D, I, D, I, D, P, P, P, ctypes.POINTER(D), ctypes.POINTER(D), P]),
         "eofa_hmc_dev": (I, [P, ctypes.POINTER(MDParams), I, D, I, P, P, P, P, P, P, ctypes.POINTER(HMCTrajInfo), P]),
         "eofa_probe_fp64_fma": (I, [ctypes.POINTER(D)]),
+        "eofa_checkpoint_write": (I, [ctypes.c_char_p, I, ctypes.POINTER(I), LL, P]),
+        "eofa_checkpoint_read": (I, [ctypes.c_char_p, I, ctypes.POINTER(I), ctypes.POINTER(LL), P]),
+        "eofa_gauge_save": (I, [P, ctypes.c_char_p, LL]),
+        "eofa_gauge_restore": (I, [P, ctypes.c_char_p, ctypes.POINTER(LL)]),
         "eofa_profile_start": (I, [P]),
         "eofa_profile_stop": (I, [P, ctypes.POINTER(Profile)]),
     }
@@ -182,6 +191,28 @@ def probe_fp64_fma() -> float:
     if rc != OK:
         raise EOFAError(rc, "eofa_probe_fp64_fma")
     return v.value
+
+
+def checkpoint_write(path, kind, field, traj=0):
+    """Write a gauge field or momenta (host canonical, shape (T, Z, Y, X, 4, 3, 3)) to a checkpoint."""
+    f = np.ascontiguousarray(field, dtype=np.complex128)
+    T, Z, Y, X = f.shape[:4]
+    dims = (ctypes.c_int * 4)(X, Y, Z, T)
+    rc = load_library().eofa_checkpoint_write(os.fsencode(path), kind, dims, int(traj), f.ctypes.data)
+    if rc != OK:
+        raise EOFAError(rc, f"eofa_checkpoint_write {path}")
+
+
+def checkpoint_read(path, kind, dims):
+    """Read a checkpoint of a lattice dims = (X, Y, Z, T); returns (field, trajectory number)."""
+    X, Y, Z, T = dims
+    f = np.empty((T, Z, Y, X, 4, 3, 3), dtype=np.complex128)
+    traj = ctypes.c_longlong()
+    rc = load_library().eofa_checkpoint_read(os.fsencode(path), kind, (ctypes.c_int * 4)(*dims), ctypes.byref(traj),
+                                             f.ctypes.data)
+    if rc != OK:
+        raise EOFAError(rc, f"eofa_checkpoint_read {path}")
+    return f, traj.value
 
 
 def rational_inv_sqrt(npoles, lmin, lmax):
@@ -423,6 +454,16 @@ class Lattice:
     def set_reliable_delta(self, delta):
         self._check(self.lib.eofa_set_reliable_delta(self.ctx, delta), "set_reliable_delta")
 
+    def set_cg_form(self, precision, form):
+        """CG iteration form at one precision: CG_FORM_AUTO, CG_FORM_FIVE or CG_FORM_SIX."""
+        self._check(self.lib.eofa_set_cg_form(self.ctx, precision, form), "set_cg_form")
+
+    def cg_form(self, precision):
+        """The form in use at one precision (CG_FORM_AUTO while undecided)."""
+        f = ctypes.c_int()
+        self._check(self.lib.eofa_get_cg_form(self.ctx, precision, ctypes.byref(f)), "get_cg_form")
+        return f.value
+
     def leapfrog_dev(self, phi, P, U, alpha, M5, m1, m2, nsteps, dtau, precision=PREC_F64, tol=1e-10):
         """Leapfrog trajectory (P, U updated in place on the device); returns (dH, H0)."""
         dH = ctypes.c_double()
@@ -494,6 +535,16 @@ class Lattice:
                                    _ptr(U) if U is not None else None, info, _stream())
         self._check(rc, "hmc_dev")
         return [info[k].as_dict() for k in range(n)]
+
+    def gauge_save(self, path, traj=0):
+        """Write the context's current links to a gauge checkpoint."""
+        self._check(self.lib.eofa_gauge_save(self.ctx, os.fsencode(path), int(traj)), "gauge_save")
+
+    def gauge_restore(self, path):
+        """Load the links of a gauge checkpoint of this lattice; returns its trajectory number."""
+        traj = ctypes.c_longlong()
+        self._check(self.lib.eofa_gauge_restore(self.ctx, os.fsencode(path), ctypes.byref(traj)), "gauge_restore")
+        return traj.value
 
     def link_update_dev(self, eps, P, U=None):
         self._check(self.lib.eofa_link_update_dev(self.ctx, eps, _ptr(P), _ptr(U) if U is not None else None,

@@ -280,3 +280,32 @@ def test_hmc_chain_pure_gauge_and_bad_arguments(eofa):
     with pytest.raises(eofa.EOFAError):
         lat.hmc_dev(_dev(np.stack(Ps[:1])), None, [0.5], None, beta=0.0)
     lat.close()
+
+
+def test_checkpoint_resume_continues_the_chain(eofa, tmp_path):
+    """Save the links after two trajectories, restore them into a new context and
+    continue both: the next trajectory gives the same dH and links bit for bit,
+    and the checkpoint holds the chain's links."""
+    import torch
+    dims = (4, 4, 4, 4)
+    U0 = inputs.gauge_field(dims, 0.3, 5)
+    Ps = [inputs.momenta(dims, 60, stream=10 + k) for k in range(3)]
+    us = [0.0, 0.0, 0.0]  # accept everything: the links move every trajectory
+    kw = dict(beta=BETA, integrator=eofa.INT_FG_QPQPQ, nsteps=2, tau=0.5)
+    lat = eofa.Lattice(dims, 4)
+    lat.gauge_load(U0)
+    U2 = torch.empty(U0.shape, dtype=torch.complex128, device="cuda")
+    lat.hmc_dev(_dev(np.stack(Ps[:2])), None, us[:2], U2, **kw)
+    path = tmp_path / "chain.ckpt"
+    lat.gauge_save(path, traj=2)
+    saved, traj = eofa.checkpoint_read(path, eofa.CKPT_GAUGE, dims)
+    assert traj == 2 and np.array_equal(saved, U2.cpu().numpy())
+    lat2 = eofa.Lattice(dims, 4)
+    assert lat2.gauge_restore(path) == 2
+    Ua, Ub = torch.empty_like(U2), torch.empty_like(U2)
+    ia = lat.hmc_dev(_dev(Ps[2][None]), None, us[2:], Ua, **kw)
+    ib = lat2.hmc_dev(_dev(Ps[2][None]), None, us[2:], Ub, **kw)
+    assert ia[0]["dH"] == ib[0]["dH"]
+    assert torch.equal(Ua, Ub)
+    lat.close()
+    lat2.close()

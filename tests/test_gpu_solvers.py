@@ -183,3 +183,39 @@ def test_solve_zero_source_returns_zero(eofa, system):
     assert info.iters == 0
     assert np.count_nonzero(x) == 0
     lat.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2])
+def test_cg_forms_reach_the_oracle_residual(eofa, prec):
+    """The five- and six-launch CG iterations, each forced, and the timed
+    choice (which switches form between iterations while it times them) all
+    reach the true residual of the oracle's EOFA system; in FP64 the forced
+    forms agree with each other to the solve tolerance.  After a solve the
+    timed choice is one of the two forms."""
+    dims, Ls = (4, 4, 4, 4), 8
+    lat, U = _setup(eofa, dims, Ls, eps=0.5)
+    b = inputs.fermion5d(dims, Ls, 7)
+    assert lat.cg_form(prec) == eofa.CG_FORM_AUTO
+    sols = {}
+    for form in (eofa.CG_FORM_FIVE, eofa.CG_FORM_SIX, eofa.CG_FORM_AUTO):
+        lat.set_cg_form(prec, form)
+        assert lat.cg_form(prec) == form
+        x, info = lat.solve(b, system=1, alpha=ALPHA, M5=M5, m1=M1, m2=M2, shift=-0.3, precision=prec,
+                            tol=1e-10)
+        Ax = oeofa.system_apply(U, x, ALPHA, M5, M1, M2, "L", -0.3, -1)
+        res = np.linalg.norm(b - Ax) / np.linalg.norm(b)
+        assert res <= 1.05e-10, (form, res)
+        assert info.iters > 10
+        sols[form] = x
+    assert lat.cg_form(prec) in (eofa.CG_FORM_FIVE, eofa.CG_FORM_SIX)
+    if prec == 0:
+        assert _rel(sols[eofa.CG_FORM_FIVE], sols[eofa.CG_FORM_SIX]) < 1e-8
+
+
+def test_cg_form_rejects_bad_arguments(eofa):
+    lat, U = _setup(eofa, (4, 4, 2, 4), 4)
+    with pytest.raises(eofa.EOFAError):
+        lat.set_cg_form(3, eofa.CG_FORM_FIVE)
+    with pytest.raises(eofa.EOFAError):
+        lat.set_cg_form(1, 2)
+    assert lat.cg_form(1) == eofa.CG_FORM_AUTO
