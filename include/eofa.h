@@ -73,9 +73,12 @@ typedef struct {
     int precision;    /* EOFA_PREC_* */
     double tol;       /* target true relative residual |b - A x| / |b| */
     int maxiter;      /* cap on inner iterations (all restarts) */
-    double delta;     /* reliable-update threshold (mixed precision); <= 0: default
-                         (1e-4 for FP32 inner storage, 0.1 for FP16, which is
-                         never below 0.05) */
+    double delta;     /* mixed precision: largest reduction of |r| between FP64
+                         reliable updates; the solver splits the way from the
+                         starting residual to the target into the fewest equal
+                         reductions no smaller than delta.  <= 0: default (5e-6 for
+                         FP32 inner storage, 0.1 for FP16, which is never below
+                         0.05) */
     int use_x0;       /* 1: x holds the initial guess on entry */
 } eofa_solve_params;
 
@@ -206,9 +209,9 @@ int eofa_pseudofermion_solutions_dev(eofa_ctx* ctx, int Ls, double alpha, double
                                      int precision, double tol, const double* phi_dev, double* chiL_dev,
                                      double* chiR_dev, double* S, eofa_solve_info info[2], void* stream);
 
-/* Reliable-update threshold delta in [0, 1) used by the solves inside
- * eofa_action / eofa_force / eofa_leapfrog_dev (0, the default, picks the
- * precision's default as in eofa_solve_params). */
+/* Reliable-update reduction delta in [0, 1) (as eofa_solve_params.delta)
+ * used by the solves inside eofa_action / eofa_force / eofa_leapfrog_dev and
+ * the HMC entry points (0, the default, picks the precision's default). */
 int eofa_set_reliable_delta(eofa_ctx* ctx, double delta);
 
 /* CG iteration form of the solves on this context at one precision

@@ -28,7 +28,7 @@
 // With mixed precision the residual is recomputed in FP64 whenever |r| has
 // dropped by the factor delta since the last recomputation (reliable
 // updates; they also reset s = A^+ r), and the solution accumulates in
-// FP64.  The stopping test is the FP64 true residual of the full,
+// FP64; delta splits the way to the target into equal segments.  The stopping test is the FP64 true residual of the full,
 // unpreconditioned system.
 #include "solver.h"
 
@@ -95,11 +95,14 @@ void Solve::setup(eofa_ctx* c, const eofa_solve_params& prm, const double* b_dev
     mixed = P.precision != EOFA_PREC_F64;
     prec = P.precision == EOFA_PREC_F64 ? P64 : (P.precision == EOFA_PREC_MIXED_F32 ? P32 : P16);
     precx = mixed ? P32 : P64;
-    // reliable-update threshold: delta <= 0 picks the default of the inner
-    // precision; FP16 storage cannot follow the residual down more than ~1e-2
-    const double auto_delta = prec == P16 ? 0.1 : 1e-4;
-    delta = (P.delta > 0 && P.delta < 1) ? P.delta : auto_delta;
-    if (prec == P16 && delta < 0.05) delta = 0.05;
+    // largest residual reduction between reliable updates: P.delta <= 0 picks
+    // the default of the inner precision.  An FP32 recursion follows the
+    // residual down by 5e-6 without costing iterations (1e-6 cost a fifth
+    // more at 24^3x64, Ls = 24); FP16 storage not much beyond ~1e-2.
+    const double auto_delta = prec == P16 ? 0.1 : 5e-6;
+    delta_max = (P.delta > 0 && P.delta < 1) ? P.delta : auto_delta;
+    if (prec == P16 && delta_max < 0.05) delta_max = 0.05;
+    delta = delta_max;
     S = P.system == EOFA_SYS_DWF ? system_dwf(P.alpha, P.M5, P.mf)
                                  : system_eofa(P.Ls, P.alpha, P.M5, P.m1, P.m2, P.system, P.shift);
     // per-solve coefficient slots so that concurrent solves on one context do not clash
@@ -184,6 +187,16 @@ bool Solve::start_cg(cudaStream_t st) {
     double rr = norm2_now(ctx, P64, r64, st);
     if (!is_finite(rr)) throw eofa_error(EOFA_ENUMERIC, "NaN/Inf in the residual");
     target = target_rel * fhn;
+    // split the reduction from |r| to the target into the fewest equal
+    // segments of at most delta_max: a reliable update ends each segment but
+    // the last, which ends at convergence (no update there, see check_value)
+    if (mixed && rr > 0 && target * target < rr) {
+        const double L = std::log(target / std::sqrt(rr));
+        const int k = std::max(1, (int)std::ceil(L / std::log(delta_max) - 1e-9));
+        delta = std::exp(L / k);
+    } else {
+        delta = delta_max;
+    }
     blas_copy(ctx, prec, r, P64, r64, st);
     if (mixed) blas_zero(ctx, precx, x, st);
     rmax = std::sqrt(rr);
@@ -306,6 +319,15 @@ void Solve::check_value(double rr, cudaStream_t st) {
     // a residual above the last recomputed one means the low-precision recursion
     // has lost track: recompute in FP64 and restart the search direction
     const bool diverging = rn > rmax;
+    if (rn < target && !diverging) {
+        // converged by the recursive residual, whose drift since the last
+        // reliable update is far below the target: finish() folds x into x_o
+        // and judges by the FP64 true residual of the full system (a CG
+        // restart follows if that is not met), so the FP64 recomputation of
+        // r here would be redundant
+        done = true;
+        return;
+    }
     if (rn < delta * rmax || rn < target || inf.iters >= P.maxiter || diverging) {
         // reliable update: x64 += x, r64 = f^ - A x64 (FP64), r = r64, s = A^+ r
         blas_copy(ctx, P64, a_o, precx, x, st);

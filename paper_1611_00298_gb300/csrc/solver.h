@@ -11,7 +11,8 @@ struct Solve {
     eofa_solve_params P;
     int prec, precx;
     bool mixed;
-    double delta;
+    double delta_max;  // largest residual reduction between reliable updates
+    double delta;      // the reduction of the current CG run (equal segments to the target)
     System5 S;
     Op5 Gi, GiT, G;
     double* red;       // reduction scratch / device scalars of this solve
