@@ -671,6 +671,11 @@ def main():
                           "fp64_true_resid": info64.true_resid,
                           "fp64_over_mixed": round(info64.seconds / mixed_s, 3)})
         hop_share = kind_ms[inner] / 1000.0 / elapsed
+        names = ["dslash_fp64", "dslash_fp32", "dslash_fp16", "local5_fp64", "local5_fp32", "local5_fp16"]
+        by_kind = {names[k]: {"launches": hop_launches[k], "ms_per_step": round(kind_ms[k] / args.steps, 2),
+                              "avg_launch_ms": round(kind_ms[k] / hop_launches[k], 4),
+                              "GB/s": round(kind_bytes[k] / (kind_ms[k] / 1000.0) / 1e9, 1) if kind_bytes[k] else None}
+                   for k in range(6) if hop_launches[k]}
         roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                     "frac": round(achieved / peak, 4), "traffic": traffic,
                     "kernel": f"fused even-odd dslash (hop + 5D-local + axpy), {'FP32' if inner == 1 else 'FP16'} "
@@ -688,6 +693,7 @@ def main():
                       f"{ {0: 'five', 1: 'six'}.get(lat.cg_form(prec), 'undecided') }-launch iteration "
                       f"({'timed' if args.cg_form == 'auto' else 'forced'})",
             "roofline": roofline, "e2e": e2e, "solve": solve, "clocks": clk, "gpu_launches": int(launches),
+            "timed_kernels": by_kind,
             "hop_launches_by_precision": {"fp64": hop_launches[0], "fp32": hop_launches[1], "fp16": hop_launches[2]},
             "action": actions[-1],
         }

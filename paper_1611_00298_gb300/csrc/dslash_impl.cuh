@@ -602,12 +602,14 @@ struct Epi {
 #ifndef EOFA_MODE1_MINB
 #define EOFA_MODE1_MINB 2
 #endif
+// (The FP64 builds spill at this cap but are bound by the FP64 FMA rate:
+// 244 registers without spills measured 5% slower at 24^3x64.)
 template <int P, int DAG, int LS, bool HASOP, int SPT, int MODE = 0>
 __global__ void __launch_bounds__(256, SPT == 2 ? 2 : (MODE == 1 ? EOFA_MODE1_MINB : (HASOP ? EOFA_DSLASH_MINB : EOFA_HOP_MINB))) dslash_kernel(
     Geom g, int par, const void* __restrict__ in, void* out, const void* __restrict__ gauge, Op5 op, const void* y,
     double a_out, double b_in, double* red, int slot, int NS, Epi ep) {
     typedef typename Field<P>::R R;
-    extern __shared__ __align__(16) unsigned char smraw[];
+    extern __shared__ __align__(128) unsigned char smraw[];
     cpx<R>* sm = reinterpret_cast<cpx<R>*>(smraw);
     const int Ls = LS > 0 ? LS : g.Ls;
     const int LsP = Ls + 1;
@@ -755,12 +757,17 @@ __global__ void __launch_bounds__(256, SPT == 2 ? 2 : (MODE == 1 ? EOFA_MODE1_MI
 
 // x' = x + c z (c = -alpha from the device scalars when use_alpha, else c0);
 // xw <- x' (if xw), |x'|^2 -> red[slot] (if red), out = a B x' (if out).
+#ifndef EOFA_LOCAL5_MINB
+#define EOFA_LOCAL5_MINB 2
+#endif
+// Up to 128 registers: at 80 the FP32 Ls = 24 build spilled 256 bytes and
+// streamed 4.9 TB/s at 24^3x64 instead of 6.4.
 template <int P, int LS>
-__global__ void __launch_bounds__(256, 3) local5_kernel(Geom g, Op5 op, const void* x, const void* z, double c0,
+__global__ void __launch_bounds__(256, EOFA_LOCAL5_MINB) local5_kernel(Geom g, Op5 op, const void* x, const void* z, double c0,
                                                      const double* sc, int it, int use_alpha, void* xw, void* out,
                                                      double a_out, double* red, int slot, int NS) {
     typedef typename Field<P>::R R;
-    extern __shared__ __align__(16) unsigned char smraw[];
+    extern __shared__ __align__(128) unsigned char smraw[];
     cpx<R>* sm = reinterpret_cast<cpx<R>*>(smraw);
     const int Ls = LS > 0 ? LS : g.Ls;
     const int LsP = Ls + 1;

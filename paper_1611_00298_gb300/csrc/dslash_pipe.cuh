@@ -133,7 +133,7 @@ __global__ void __launch_bounds__(256, EOFA_PIPE_MINB) dslash_pipe_kernel(
     Geom g, int par, const void* __restrict__ in, void* out, const void* __restrict__ gauge, Op5 op, const void* y,
     double a_out, double b_in, double* red, int slot, int NS) {
     typedef typename Field<P>::R R;
-    extern __shared__ __align__(16) unsigned char smraw[];
+    extern __shared__ __align__(128) unsigned char smraw[];
     const int nt = blockDim.x;
     unsigned char* st = smraw;
     cpx<R>* sm = reinterpret_cast<cpx<R>*>(smraw + pipe_stage_bytes<P>(PIPE, nt));

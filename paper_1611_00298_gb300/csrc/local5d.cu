@@ -57,7 +57,7 @@ template <int P>
 __global__ void op5_kernel(Geom g, Op5 op, int NS, const void* x, const void* y,
                            void* out) {
     typedef typename Field<P>::R R;
-    extern __shared__ __align__(16) unsigned char smraw[];
+    extern __shared__ __align__(128) unsigned char smraw[];
     cpx<R>* sm = reinterpret_cast<cpx<R>*>(smraw);
     const int Ls = g.Ls, LsP = g.Ls + 1;
     long long n5 = (long long)g.Vh * Ls;

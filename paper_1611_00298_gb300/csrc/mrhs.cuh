@@ -110,7 +110,7 @@ __global__ void __launch_bounds__(256, HASOP ? EOFA_DSLASH_MINB : EOFA_HOP_MINB)
                      int RB, const void* __restrict__ gauge, double a_out, double b_in, int slot, int NS, int it,
                      int slot2) {
     typedef typename Field<P>::R R;
-    extern __shared__ __align__(16) unsigned char smraw[];
+    extern __shared__ __align__(128) unsigned char smraw[];
     const int Ls = LS > 0 ? LS : g.Ls;
     const int LsP = Ls + 1;
     const int r0 = blockIdx.y * RB;
