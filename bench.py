@@ -654,8 +654,9 @@ def main():
 
         mixed_s = statistics.mean(i[0]["seconds"] for i in infos)
         solve = {"system": "chi_L = H(m1)^-1 Omega_- P_- phi (Eq. (8), a = 0)",
-                 "mixed_f32_seconds": round(mixed_s, 4),
+                 f"mixed_{args.precision}_seconds": round(mixed_s, 4),
                  "mixed_iters": infos[-1][0]["iters"], "mixed_reliable_updates": infos[-1][0]["reliable_updates"],
+                 "mixed_fp32_updates": infos[-1][0]["low_updates"],
                  "mixed_true_resid": infos[-1][0]["true_resid"]}
         if not args.no_fp64:
             b = torch.empty(lat.V * Ls * 12, dtype=torch.complex128, device="cuda")

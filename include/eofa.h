@@ -88,6 +88,8 @@ typedef struct {
     double true_resid;     /* FP64 |b - A x| / |b| of the full (unpreconditioned) system */
     double seconds;        /* wall time of the solve */
     int status;            /* EOFA_OK or the failure */
+    int low_updates;       /* FP32 residual recomputations between the FP64 ones
+                              (EOFA_PREC_MIXED_F16 only) */
 } eofa_solve_info;
 
 /* Create a context for one lattice.  dims: {X, Y, Z, T}, all even and >= 2;

@@ -16,11 +16,13 @@
 // runs out of iterations.  Only then does the host look at the group: it
 // does the reliable updates and the true-residual checks of solver.cu,
 // retires converged systems (re-capturing the graph for the smaller set)
-// and relaunches.  Groups run concurrently on their own streams; the host
-// services whichever group's graph has finished.
+// and relaunches.  Lock-step groups run concurrently on their own streams,
+// single-system groups one after another beside them; the host services
+// whichever group's graph has finished.
 #include "mrhs.h"
 #include "solver.h"
 
+#include <algorithm>
 #include <chrono>
 #include <cstdio>
 #include <cstdlib>
@@ -105,6 +107,7 @@ struct Group {
     std::vector<int> last;        // systems of the last launch (graph or eager chunk)
     bool running = false;
     bool finished = false;
+    bool pending = false;         // single: waits until the single group before it has finished
     // diagnostics (EOFA_BATCH_LOG=1): host visits, graph builds, host seconds
     int visits = 0, builds = 0;
     double host_s = 0.0, build_s = 0.0;
@@ -334,9 +337,39 @@ extern "C" int eofa_solve_batched(eofa_ctx* const* ctxs, int n, const eofa_solve
                 if (!sv[i].trivial) sv[i].start_cg(g.st);
             }
         }
+        // Single groups run one at a time, each alone filling the GPU with its
+        // fields resident in L2 for its whole device loop, while the lock-step
+        // groups of the small lattices run beside them (all single groups at
+        // once, 8 systems at 16^3 x 32 x 16 took 3.6 s against 2.7 s for the
+        // same solves one after another).
+        std::vector<Group*> singles;
+        std::map<eofa_ctx*, bool> tuned_ctx;
+        for (auto& gp : groups)
+            if (gp->single) {
+                gp->pending = !singles.empty();
+                singles.push_back(gp.get());
+                // the eager first chunk (kernel autotuning) is needed once per context
+                if (tuned_ctx[gp->ctx]) gp->eager_done = true;
+                tuned_ctx[gp->ctx] = true;
+            }
+        // the single groups are the critical path: the host services them first
+        std::stable_partition(groups.begin(), groups.end(), [](const std::unique_ptr<Group>& g) { return g->single; });
+        size_t next_single = 1;
+        auto start_next_single = [&]() {
+            while (next_single < singles.size()) {
+                Group* ng = singles[next_single++];
+                ng->pending = false;
+                errctx = ng->ctx;
+                ng->finished = !service_group(*ng, sv, finished, xdev);
+                if (!ng->finished) break;
+            }
+        };
         for (auto& gp : groups) {
+            // (a single group started by start_next_single is running or finished already)
+            if (gp->pending || gp->running || gp->finished) continue;
             errctx = gp->ctx;
             gp->finished = !service_group(*gp, sv, finished, xdev);
+            if (gp->single && gp->finished) start_next_single();
         }
         for (;;) {
             bool any = false, progressed = false;
@@ -344,7 +377,7 @@ extern "C" int eofa_solve_batched(eofa_ctx* const* ctxs, int n, const eofa_solve
                 Group& g = *gp;
                 if (g.finished) continue;
                 any = true;
-                if (!g.running) continue;
+                if (g.pending || !g.running) continue;
                 cudaError_t q = cudaEventQuery(g.done);
                 if (q == cudaErrorNotReady) continue;
                 EOFA_CUDA(q);
@@ -355,6 +388,7 @@ extern "C" int eofa_solve_batched(eofa_ctx* const* ctxs, int n, const eofa_solve
                 collect_group(g, sv);
                 g.finished = !service_group(g, sv, finished, xdev);
                 g.host_s += std::chrono::duration<double>(std::chrono::steady_clock::now() - th).count();
+                if (g.single && g.finished) start_next_single();
             }
             if (!any) break;
             if (!progressed) std::this_thread::sleep_for(std::chrono::microseconds(20));
@@ -394,8 +428,9 @@ extern "C" int eofa_solve_batched(eofa_ctx* const* ctxs, int n, const eofa_solve
         if (g.st) cudaStreamSynchronize(g.st);
         destroy_graph(g);
         if (g.done) cudaEventDestroy(g.done);
-        if (g.st) cudaStreamDestroy(g.st);
         if (g.ctl_host) cudaFreeHost(g.ctl_host);
     }
+    for (auto& gp : groups)
+        if (gp->st) cudaStreamDestroy(gp->st);
     return rc;
 }

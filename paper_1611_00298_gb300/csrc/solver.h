@@ -12,6 +12,9 @@ struct Solve {
     int prec, precx;
     bool mixed;
     double delta_max;  // largest residual reduction between reliable updates
+    bool two_level;    // FP16 inner storage: FP32 reliable updates between the FP64 ones
+    double delta64, rmax64;       // two-level: reduction between FP64 updates, residual of the last one
+    void *ra32, *rt32, *te32;     // two-level: FP32 anchor residual, FP32 residual, FP32 workspace
     double delta;      // the reduction of the current CG run (equal segments to the target)
     System5 S;
     Op5 Gi, GiT, G;

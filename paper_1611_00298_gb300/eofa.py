@@ -88,7 +88,7 @@ class HMCTrajInfo(ctypes.Structure):
 
 class SolveInfo(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("reliable_updates", ctypes.c_int), ("true_resid", ctypes.c_double),
-                ("seconds", ctypes.c_double), ("status", ctypes.c_int)]
+                ("seconds", ctypes.c_double), ("status", ctypes.c_int), ("low_updates", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -219,3 +219,20 @@ def test_cg_form_rejects_bad_arguments(eofa):
     with pytest.raises(eofa.EOFAError):
         lat.set_cg_form(1, 2)
     assert lat.cg_form(1) == eofa.CG_FORM_AUTO
+
+
+def test_fp16_solve_recomputes_mostly_in_fp32(eofa):
+    """FP16 inner storage: the residual is recomputed in FP32 at every ~0.1
+    reduction (relative to the last FP64 residual) and in FP64 at every ~1e-4
+    reduction; the solve still reaches the oracle's true residual.  FP32
+    inner storage recomputes in FP64 only."""
+    dims, Ls = (4, 4, 4, 4), 8
+    lat, U = _setup(eofa, dims, Ls)
+    b = inputs.fermion5d(dims, Ls, 5)
+    x, info = lat.solve(b, system=eofa.SYS_DWF, alpha=2.0, M5=M5, mf=M1, precision=2, tol=1e-10)
+    res = np.linalg.norm(b - dwf.dwf(U, x, 2.0, M5, M1, -1)) / np.linalg.norm(b)
+    assert res <= 1.05e-10, res
+    assert 1 <= info.reliable_updates <= 4, info.reliable_updates
+    assert info.low_updates >= 4 and info.low_updates > info.reliable_updates, info.low_updates
+    x, info = lat.solve(b, system=eofa.SYS_DWF, alpha=2.0, M5=M5, mf=M1, precision=1, tol=1e-10)
+    assert info.low_updates == 0
