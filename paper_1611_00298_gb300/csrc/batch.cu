@@ -6,9 +6,9 @@
 // Systems on the same (small) lattice and with the same inner precision
 // form a group (at most MR_MAX systems); a system on a large lattice is a
 // group of its own (MR_SINGLE_SITES).  A group iterates its systems in lock
-// step with the multi-system kernels of mrhs.cuh: the five launches of the
-// CG iteration of solver.cu, each for all of them, each link row and
-// neighbour index fetched once for the whole group.  The CG loop of a group runs on the device: a CUDA graph
+// step with the multi-system kernels of mrhs.cuh: the five-launch form of
+// the CG iteration of solver.cu, each launch for all of them, each link row
+// and neighbour index fetched once for the whole group.  The CG loop of a group runs on the device: a CUDA graph
 // holds one WHILE conditional node whose body is K CG iterations of every
 // active system followed by a one-block decision kernel; the kernel reads
 // each system's |r|^2 and keeps the loop going until some system has
