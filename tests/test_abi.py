@@ -105,3 +105,33 @@ def test_check_device_rejects_null_context(libpath):
     from paper_1611_00298_gb300 import eofa
     lib = eofa.load_library(libpath)
     assert lib.eofa_check_device(None, None) == eofa.EINVAL
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """Every ctypes structure of the binding has the size and field offsets of
+    its C struct in include/eofa.h (compiled here with the host C compiler),
+    so that a field added on one side only is caught without a GPU."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    from paper_1611_00298_gb300 import eofa as e
+    pairs = {"eofa_solve_params": e.SolveParams, "eofa_solve_info": e.SolveInfo, "eofa_md_params": e.MDParams,
+             "eofa_md_info": e.MDInfo, "eofa_hmc_traj_info": e.HMCTrajInfo, "eofa_profile": e.Profile}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "eofa.h"', "int main(void) {"]
+    for cname, cls in pairs.items():
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f, _ in cls._fields_:
+            lines.append(f'  printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for cname, cls in pairs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(cls), cname
+        for f, _ in cls._fields_:
+            assert got[(cname, f)] == getattr(cls, f).offset, (cname, f)
