@@ -343,14 +343,16 @@ extern "C" int eofa_solve_batched(eofa_ctx* const* ctxs, int n, const eofa_solve
         // once, 8 systems at 16^3 x 32 x 16 took 3.6 s against 2.7 s for the
         // same solves one after another).
         std::vector<Group*> singles;
-        std::map<eofa_ctx*, bool> tuned_ctx;
+        std::map<std::pair<eofa_ctx*, int>, bool> tuned;
         for (auto& gp : groups)
             if (gp->single) {
                 gp->pending = !singles.empty();
                 singles.push_back(gp.get());
-                // the eager first chunk (kernel autotuning) is needed once per context
-                if (tuned_ctx[gp->ctx]) gp->eager_done = true;
-                tuned_ctx[gp->ctx] = true;
+                // the eager first chunk (kernel autotuning, CG form) is needed
+                // once per context and precision
+                const auto key = std::make_pair(gp->ctx, gp->prec);
+                if (tuned[key]) gp->eager_done = true;
+                tuned[key] = true;
             }
         // the single groups are the critical path: the host services them first
         std::stable_partition(groups.begin(), groups.end(), [](const std::unique_ptr<Group>& g) { return g->single; });
