@@ -33,6 +33,7 @@
 // the last FP64 residual, and an FP64 one follows every reduction by ~1e-4.  The stopping test is the FP64 true residual of the full,
 // unpreconditioned system.
 #include "solver.h"
+#include "reliable.h"
 
 #include <algorithm>
 
@@ -206,12 +207,7 @@ bool Solve::start_cg(cudaStream_t st) {
     // split the reduction from |r| to the target into the fewest equal
     // segments of at most delta_max: a reliable update ends each segment but
     // the last, which ends at convergence (no update there, see check_value)
-    auto segment = [&](double dmax) {
-        if (!(mixed && rr > 0 && target * target < rr)) return dmax;
-        const double L = std::log(target / std::sqrt(rr));
-        const int k = std::max(1, (int)std::ceil(L / std::log(dmax) - 1e-9));
-        return std::exp(L / k);
-    };
+    auto segment = [&](double dmax) { return mixed ? equal_segment_reduction(std::sqrt(rr), target, dmax) : dmax; };
     delta = segment(delta_max);
     if (two_level) {
         // FP16 inner storage: FP32 recomputations every delta, FP64 ones every
